@@ -1,0 +1,387 @@
+"""Plain FP64 CPU oracle for the FDAS correlation hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference leg of ``bench.py`` may import or run anything in
+``oracle/``; the product (the CUDA library and its binding) never does.
+
+It computes, slowly and by definition, what the GPU path computes fast:
+
+* ``template_response``  R_z(d), the predicted normalised Fourier response of
+  a constant-fdot signal at offset d from its mid-observation bin (Section 2,
+  Eqs. 22-23; the paper cites the closed form rather than printing it).
+* ``real_spectrum``      the real-to-complex DFT of the series (Section 4.1,
+  DFT sign convention of Section 4.2), DC zeroed, Nyquist dropped.
+* ``normalise``          block running-median power normalisation (Section 3).
+* ``correlate``          the matched-filter correlation of Eq. 23 as a direct
+  tap sum -- no FFT and no overlap-save (Section 3 explains overlap-save only
+  as a fast way to evaluate this same sum).
+* ``power_plane``        full-bin power and interbinned half-bin power
+  (Eq. "f-interp", Section 3).
+* ``threshold``          candidates P > T, with the local-maximum flag.
+
+Readings of the paper that this file relies on (each also listed in the
+design notes):
+
+1. R_z(d) = int_0^1 exp(i 2 pi (z u^2/2 - (d + z/2) u)) du: a unit chirp
+   centred on its mid-observation frequency.  It is the one centring under
+   which the +/-z conjugate symmetry used in Section 4.2 holds exactly at
+   integer offsets; no further normalisation (sum_d |R_z(d)|^2 -> 1).
+2. Template half-width h(z) = ceil(|z|/2) + 8 taps.
+3. DC bin zeroed, Nyquist bin dropped: n samples -> n/2 bins.
+4. Median filter: non-overlapping blocks of ``block`` bins (the tail block
+   takes the remainder); lower median (rank floor((len-1)/2)) of |X|^2;
+   scale sqrt(median / ln 2), because the median of Exp(mu) is mu ln 2, so
+   normalised noise power has mean 1.  A block whose median is 0 is set to 0.
+5. Interbinning F_{r+1/2} = (pi/4)(F_r - F_{r+1}); the last half bin of a
+   row (no F_{r+1}) is 0.
+6. Plane layout: row j is z_j = zmin + j zstep; column 2r is the full bin r,
+   column 2r+1 the half bin r + 1/2 (interbin) -- or column r (no interbin).
+
+Parity pins for every function here live in tests/test_oracle.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+from scipy.special import fresnel
+
+__all__ = [
+    "half_width", "z_grid", "template_response", "template_taps", "kernel_spectrum",
+    "real_spectrum", "normalise", "block_medians", "correlate", "correlate_points",
+    "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
+    "search", "oracle_threads", "PEAK_FLAG",
+]
+
+PEAK_FLAG = 1
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_tapsum.so")
+_lib = None
+_lock = threading.Lock()
+
+
+# --------------------------------------------------------------------------
+# build / load the C tap sum (plain gcc + OpenMP)
+# --------------------------------------------------------------------------
+def build(force: bool = False) -> str:
+    """Compile oracle/tapsum.c into oracle/_tapsum.so (plain C, -O2, OpenMP)."""
+    src = os.path.join(_HERE, "tapsum.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+            lp = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_tapsum.argtypes = [dp, ctypes.c_int64, dp, ip, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, dp]
+            lib.oracle_tapsum.restype = None
+            lib.oracle_tapsum_points.argtypes = [dp, ctypes.c_int64, dp, ip, ctypes.c_int32,
+                                                 ip, lp, ctypes.c_int64, dp]
+            lib.oracle_tapsum_points.restype = None
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def oracle_threads() -> int:
+    """Number of OpenMP threads the tap sum runs on."""
+    return int(_load().oracle_num_threads())
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+# --------------------------------------------------------------------------
+# templates (Section 2, Eqs. 22-23)
+# --------------------------------------------------------------------------
+def half_width(z: float) -> int:
+    """Template half-width in taps: ceil(|z|/2) + 8 (reading 2)."""
+    return int(math.ceil(abs(float(z)) / 2.0)) + 8
+
+
+def z_grid(zmin: int, zmax: int, zstep: int) -> np.ndarray:
+    """Plane row j holds z_j = zmin + j*zstep, j = 0..K-1."""
+    K = (int(zmax) - int(zmin)) // int(zstep) + 1
+    return (int(zmin) + int(zstep) * np.arange(K)).astype(np.float64)
+
+
+def _response_quadrature(z: float, d: np.ndarray) -> np.ndarray:
+    """R_z(d) by composite 16-point Gauss-Legendre quadrature of its definition.
+
+    Used for 0 < |z| < 0.5, where the Fresnel closed form loses digits to the
+    large cancelling phases.  Panels are sized to at most one cycle of the
+    integrand.
+    """
+    x, w = np.polynomial.legendre.leggauss(16)
+    out = np.empty(d.shape, np.complex128)
+    for idx, dd in np.ndenumerate(d):
+        panels = int(math.ceil(abs(dd) + abs(z) + 2.0))
+        edges = np.linspace(0.0, 1.0, panels + 1)
+        mid = 0.5 * (edges[1:] + edges[:-1])
+        half = 0.5 * (edges[1:] - edges[:-1])
+        u = (mid[:, None] + half[:, None] * x[None, :]).ravel()
+        ww = (half[:, None] * w[None, :]).ravel()
+        ph = z * u * u / 2.0 - (dd + z / 2.0) * u
+        out[idx] = np.sum(ww * np.exp(2j * np.pi * ph))
+    return out
+
+
+def template_response(z: float, d) -> np.ndarray:
+    """R_z(d) = int_0^1 exp(i 2 pi (z u^2/2 - (d + z/2) u)) du  (complex128).
+
+    Closed form (z != 0), completing the square with q = -(d + z/2):
+        R = exp(-i pi q^2/z) [ (C(Y)-C(X)) + i sgn(z) (S(Y)-S(X)) ] / sqrt(2|z|),
+        X = sqrt(2|z|) q/z,  Y = sqrt(2|z|) (1 + q/z),
+    with C, S the Fresnel integrals int_0^x cos/sin(pi t^2/2) dt
+    (scipy.special.fresnel is the library primitive).  z = 0 gives
+    exp(-i pi d) sinc(d), a Kronecker delta at integer d.
+    """
+    z = float(z)
+    d = np.asarray(d, dtype=np.float64)
+    if z == 0.0:
+        return np.exp(-1j * np.pi * d) * np.sinc(d)
+    if abs(z) < 0.5:
+        return _response_quadrature(z, d)
+    q = -(d + 0.5 * z)
+    s = math.sqrt(2.0 * abs(z))
+    X = s * q / z
+    Y = s * (1.0 + q / z)
+    SX, CX = fresnel(X)          # scipy returns (S, C)
+    SY, CY = fresnel(Y)
+    sg = 1.0 if z > 0 else -1.0
+    inner = (CY - CX) + 1j * sg * (SY - SX)
+    return np.exp(-1j * np.pi * q * q / z) * inner / s
+
+
+def template_taps(zs, hmax: int | None = None):
+    """R[k, hmax + d] = R_{z_k}(d) for |d| <= h(z_k) (zero beyond), and h[k]."""
+    zs = np.asarray(zs, np.float64)
+    h = np.array([half_width(z) for z in zs], np.int32)
+    if hmax is None:
+        hmax = int(h.max()) if len(h) else 0
+    R = np.zeros((len(zs), 2 * hmax + 1), np.complex128)
+    for k, z in enumerate(zs):
+        d = np.arange(-h[k], h[k] + 1)
+        R[k, hmax - h[k]: hmax + h[k] + 1] = template_response(z, d)
+    return R, h
+
+
+def kernel_spectrum(z: float, L: int) -> np.ndarray:
+    """H_z[k], k = 0..L-1, natural order: the length-L FIR kernel of template z.
+
+    The kernel g[j] = conj(R_z(-j)) for |j| <= h is placed so that it is
+    centred at bin 0 (j >= 0 at the start of the array, j < 0 wrapped to the
+    end, zeros between: Section 3, Fig. 1); H = FFT_L(g) / L, the 1/L of the
+    inverse transform being folded in here.  Circular convolution with g is
+    then the correlation of Eq. 23.
+    """
+    h = half_width(z)
+    g = np.zeros(L, np.complex128)
+    j = np.arange(-h, h + 1)
+    g[j % L] = np.conj(template_response(z, -j))
+    return np.fft.fft(g) / L
+
+
+# --------------------------------------------------------------------------
+# front end (Sections 3 and 4.1): real FFT + running-median normalisation
+# --------------------------------------------------------------------------
+def real_spectrum(x) -> np.ndarray:
+    """X_k = sum_n x_n exp(-i 2 pi k n / n_samples), k = 0..n/2-1; X_0 := 0.
+
+    numpy's FFT is the library primitive.  The Nyquist bin is dropped.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    X = np.fft.rfft(x)[: n // 2].copy()
+    if n // 2 > 0:
+        X[0] = 0.0
+    return X
+
+
+def block_medians(X, block: int = 1024) -> np.ndarray:
+    """Lower median of |X|^2 over each block of ``block`` bins (reading 4)."""
+    P = np.abs(np.asarray(X)) ** 2
+    nb = P.shape[0]
+    nblk = (nb + block - 1) // block
+    med = np.empty(nblk, np.float64)
+    for b in range(nblk):
+        seg = P[b * block: (b + 1) * block]
+        rank = (seg.shape[0] - 1) // 2
+        med[b] = np.partition(seg, rank)[rank]
+    return med
+
+
+def normalise(X, block: int = 1024) -> np.ndarray:
+    """A_k = X_k / sqrt(median_b / ln 2) for k in block b (0 if median_b = 0)."""
+    X = np.asarray(X, dtype=np.complex128)
+    med = block_medians(X, block)
+    A = np.zeros_like(X)
+    for b, m in enumerate(med):
+        if m > 0.0:
+            sl = slice(b * block, (b + 1) * block)
+            A[sl] = X[sl] / math.sqrt(m / math.log(2.0))
+    return A
+
+
+# --------------------------------------------------------------------------
+# correlation (Eq. 23) and power / interbinning (Eq. f-interp)
+# --------------------------------------------------------------------------
+def correlate(A, zs, r0: int = 0, nr: int | None = None) -> np.ndarray:
+    """F[k, i] = sum_{|d| <= h_k} A[r0+i+d] conj(R_{z_k}(d)), A = 0 outside [0, nb)."""
+    A = np.ascontiguousarray(np.asarray(A, np.complex128))
+    nb = A.shape[0]
+    if nr is None:
+        nr = nb - r0
+    R, h = template_taps(zs)
+    R = np.ascontiguousarray(R)
+    K, hmax = R.shape[0], (R.shape[1] - 1) // 2
+    F = np.zeros((K, nr), np.complex128)
+    if K and nr > 0:
+        _load().oracle_tapsum(_ptr(A.view(np.float64), ctypes.c_double), nb,
+                              _ptr(R.view(np.float64), ctypes.c_double),
+                              _ptr(h, ctypes.c_int32), K, hmax, int(r0), int(nr),
+                              _ptr(F.view(np.float64), ctypes.c_double))
+    return F
+
+
+def correlate_points(A, zs, zi, r) -> np.ndarray:
+    """F at scattered points: template index zi[p], bin r[p]."""
+    A = np.ascontiguousarray(np.asarray(A, np.complex128))
+    zi = np.ascontiguousarray(np.asarray(zi, np.int32))
+    r = np.ascontiguousarray(np.asarray(r, np.int64))
+    R, h = template_taps(zs)
+    R = np.ascontiguousarray(R)
+    hmax = (R.shape[1] - 1) // 2
+    F = np.zeros(zi.shape[0], np.complex128)
+    if zi.shape[0]:
+        _load().oracle_tapsum_points(_ptr(A.view(np.float64), ctypes.c_double), A.shape[0],
+                                     _ptr(R.view(np.float64), ctypes.c_double),
+                                     _ptr(h, ctypes.c_int32), hmax, _ptr(zi, ctypes.c_int32),
+                                     _ptr(r, ctypes.c_int64), zi.shape[0],
+                                     _ptr(F.view(np.float64), ctypes.c_double))
+    return F
+
+
+HALF_BIN_SCALE = (math.pi / 4.0) ** 2
+
+
+def power_plane(F, interbin: bool = True, last_is_end: bool = True) -> np.ndarray:
+    """Plane from correlated amplitudes F[k, r] (r = 0..nr-1).
+
+    interbin: columns 2r = |F_r|^2 and 2r+1 = (pi/4)^2 |F_r - F_{r+1}|^2.
+    If ``last_is_end`` the final half bin (no F_{r+1}) is 0; otherwise F must
+    carry one extra column (r = nr) used only for the last half bin.
+    """
+    F = np.asarray(F)
+    if not interbin:
+        return np.abs(F) ** 2
+    if last_is_end:
+        nr = F.shape[1]
+        nxt = np.concatenate([F[:, 1:], np.zeros((F.shape[0], 1), F.dtype)], axis=1)
+    else:
+        nr = F.shape[1] - 1
+        nxt = F[:, 1:]
+    P = np.empty((F.shape[0], 2 * nr), np.float64)
+    P[:, 0::2] = np.abs(F[:, :nr]) ** 2
+    P[:, 1::2] = HALF_BIN_SCALE * np.abs(F[:, :nr] - nxt) ** 2
+    if last_is_end and nr:
+        P[:, -1] = 0.0
+    return P
+
+
+def plane(A, zs, interbin: bool = True) -> np.ndarray:
+    """The whole f-fdot power plane, K x (2nb or nb)."""
+    return power_plane(correlate(A, zs), interbin, last_is_end=True)
+
+
+def plane_window(A, zs, r0: int, nr: int, interbin: bool = True) -> np.ndarray:
+    """Plane columns for bins r0..r0+nr-1 (2nr columns with interbinning)."""
+    nb = np.asarray(A).shape[0]
+    if not interbin:
+        return power_plane(correlate(A, zs, r0, nr), False)
+    ends = r0 + nr >= nb
+    extra = 0 if ends else 1
+    F = correlate(A, zs, r0, nr + extra)
+    return power_plane(F, True, last_is_end=ends)
+
+
+def plane_points(A, zs, zi, col, interbin: bool = True) -> np.ndarray:
+    """Plane values at scattered (row zi[p], column col[p])."""
+    A = np.asarray(A)
+    nb = A.shape[0]
+    zi = np.asarray(zi, np.int64)
+    col = np.asarray(col, np.int64)
+    if not interbin:
+        return np.abs(correlate_points(A, zs, zi, col)) ** 2
+    r = col // 2
+    half = (col % 2) == 1
+    Fr = correlate_points(A, zs, zi, r)
+    out = np.abs(Fr) ** 2
+    if half.any():
+        rn = np.minimum(r[half] + 1, nb - 1)
+        Fn = correlate_points(A, zs, zi[half], rn)
+        ph = HALF_BIN_SCALE * np.abs(Fr[half] - Fn) ** 2
+        ph[r[half] + 1 >= nb] = 0.0
+        out[half] = ph
+    return out
+
+
+# --------------------------------------------------------------------------
+# candidates
+# --------------------------------------------------------------------------
+def peak_flags(P, rows, cols) -> np.ndarray:
+    """1 where (row, col) is a local maximum over its 8 neighbours.
+
+    Ties go to the lower (row, col): the point must be strictly above every
+    neighbour that precedes it in row-major order and at least equal to every
+    neighbour after it.
+    """
+    P = np.asarray(P)
+    K, W = P.shape
+    out = np.zeros(len(rows), np.int32)
+    for i, (a, c) in enumerate(zip(rows, cols)):
+        v = P[a, c]
+        ok = True
+        for da in (-1, 0, 1):
+            for dc in (-1, 0, 1):
+                if da == 0 and dc == 0:
+                    continue
+                b, e = a + da, c + dc
+                if b < 0 or b >= K or e < 0 or e >= W:
+                    continue
+                w = P[b, e]
+                before = (b, e) < (a, c)
+                if (before and not v > w) or ((not before) and not v >= w):
+                    ok = False
+        out[i] = PEAK_FLAG if ok else 0
+    return out
+
+
+def threshold(P, thr: float, flags: bool = True):
+    """Candidates with P > thr, sorted by (row, col): arrays (rows, cols, power, flags)."""
+    P = np.asarray(P)
+    rows, cols = np.nonzero(P > thr)
+    pw = P[rows, cols]
+    fl = peak_flags(P, rows, cols) if flags else np.zeros(len(rows), np.int32)
+    return rows.astype(np.int32), cols.astype(np.int32), pw, fl
+
+
+def search(x, zmin, zmax, zstep, block=1024, thr=20.0, interbin=True):
+    """Whole path on the CPU: spectrum -> normalise -> plane -> candidates."""
+    A = normalise(real_spectrum(x), block)
+    zs = z_grid(zmin, zmax, zstep)
+    P = plane(A, zs, interbin)
+    return A, P, threshold(P, thr)

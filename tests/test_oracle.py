@@ -1,0 +1,266 @@
+"""Pins for the FP64 oracle: each checks it against something other than itself.
+
+Mathematics and the paper fix every expected value here: the defining
+integral (evaluated by an adaptive library integrator, not the oracle's
+Fresnel form), closed forms, Parseval, brute-force sums, a different
+algorithm (overlap-save with FFTs) for the same correlation, and the
+amplitude-loss figures printed in Section 3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle.fdas_oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- templates
+def _integral(z, d):
+    """R_z(d) by scipy.integrate.quad of the real and imaginary parts."""
+    ph = lambda u: 2 * math.pi * (z * u * u / 2 - (d + z / 2) * u)  # noqa: E731
+    kw = dict(limit=2000, epsabs=1e-14, epsrel=1e-13)
+    re = integrate.quad(lambda u: math.cos(ph(u)), 0, 1, **kw)[0]
+    im = integrate.quad(lambda u: math.sin(ph(u)), 0, 1, **kw)[0]
+    return re + 1j * im
+
+
+@pytest.mark.parametrize("z", [2.0, 10.0, 64.0, 200.0, -200.0, -7.3, 0.3, -0.05, 3.7])
+def test_template_matches_defining_integral(z):
+    ds = [-108, -40, -3, -1, 0, 0.37, 1, 2.5, 40, 108]
+    got = O.template_response(z, np.array(ds, float))
+    ref = np.array([_integral(z, d) for d in ds])
+    assert np.abs(got - ref).max() < 1e-10
+
+
+def test_template_z0_is_delta_and_sinc():
+    d = np.arange(-20, 21)
+    R = O.template_response(0.0, d)
+    assert np.abs(R - (d == 0)).max() < 1e-15
+    f = np.array([0.25, 0.5, -0.5, 1.5])
+    ref = (1 - np.exp(-2j * np.pi * f)) / (2j * np.pi * f)   # int_0^1 e^{-i2pi f u} du
+    assert np.abs(O.template_response(0.0, f) - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("z", [2.0, 17.0, 200.0])
+def test_template_plus_minus_z_symmetry(z):
+    # integer offsets: R_{-z}(d) = conj(R_z(d)) (the symmetry used in Section 4.2)
+    d = np.arange(-120, 121)
+    assert np.abs(O.template_response(-z, d) - np.conj(O.template_response(z, d))).max() < 1e-12
+    # fractional offsets pick up exp(-i 2 pi d)  (u -> 1-u in the integral)
+    f = np.array([-3.3, 0.25, 7.5])
+    lhs = O.template_response(-z, f)
+    rhs = np.exp(-2j * np.pi * f) * np.conj(O.template_response(z, f))
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+@pytest.mark.parametrize("z", [0.0, 6.0, 200.0])
+def test_template_parseval_and_sum(z):
+    # R_z(d) are the Fourier-series coefficients of exp(i pi z (u^2 - u)) on [0,1]:
+    # sum |R|^2 = int |f|^2 = 1 and sum R = f(0) = 1.  f' jumps by 2 i pi z at
+    # the ends, so R_z(d) ~ -i z / (2 pi d^2) and the tail beyond |d| = D sums
+    # to about i z / (pi D), which the partial sum misses.
+    D = 20000
+    d = np.arange(-D, D + 1)
+    R = O.template_response(z, d)
+    assert abs(np.sum(np.abs(R) ** 2) - 1.0) < 2e-5
+    assert abs(np.sum(R) - (1.0 - 1j * z / (math.pi * D))) < 1e-6
+
+
+def test_half_width():
+    assert [O.half_width(z) for z in (0, 1, 2, -21, 200, -200)] == [8, 9, 9, 19, 108, 108]
+    assert list(O.z_grid(-20, 20, 2)[:3]) == [-20, -18, -16] and len(O.z_grid(-200, 200, 2)) == 201
+
+
+# ---------------------------------------------------------------- front end
+def test_real_spectrum_bruteforce_and_sign():
+    rng = np.random.default_rng(0)
+    n = 64
+    x = rng.standard_normal(n)
+    k = np.arange(n // 2)[:, None]
+    t = np.arange(n)[None, :]
+    ref = (np.exp(-2j * np.pi * k * t / n) * x[None, :]).sum(1)
+    ref[0] = 0
+    assert np.abs(O.real_spectrum(x) - ref).max() < 1e-12
+    # sign convention: sin(2 pi k0 t/n) -> X_k0 = -i n/2
+    s = np.sin(2 * np.pi * 5 * np.arange(n) / n)
+    X = O.real_spectrum(s)
+    assert abs(X[5] - (-0.5j * n)) < 1e-12 and np.abs(np.delete(X, 5)).max() < 1e-12
+
+
+def test_real_spectrum_parseval():
+    rng = np.random.default_rng(1)
+    n = 4096
+    x = rng.standard_normal(n)
+    x -= x.mean()
+    X = np.fft.fft(x)
+    # sum over the half spectrum (bins 1..n/2-1) is half the energy minus Nyquist
+    half = np.sum(np.abs(O.real_spectrum(x)) ** 2)
+    total = n * np.sum(x ** 2)
+    assert abs(2 * half + abs(X[n // 2]) ** 2 - total) < 1e-8 * total
+
+
+def test_block_median_rank_and_tail():
+    X = np.sqrt(np.array([3.0, 1.0, 2.0, 5.0, 9.0, 4.0, 7.0]))
+    # blocks of 4: [3,1,2,5] -> sorted 1,2,3,5 -> rank 1 -> 2 ; tail [9,4,7] -> 4,7,9 -> rank 1 -> 7
+    assert np.allclose(O.block_medians(X, 4), [2.0, 7.0])
+    A = O.normalise(X, 4)
+    assert np.allclose(A[:4], X[:4] / math.sqrt(2.0 / math.log(2)))
+    assert np.all(O.normalise(np.zeros(8), 4) == 0)
+
+
+def test_normalised_noise_is_unit_exponential():
+    x = synth.make_series(1 << 17, (), seed=11)
+    A = O.normalise(O.real_spectrum(x), 1024)
+    P = np.abs(A[1024:]) ** 2
+    # the median of each block is ln 2 by construction; Exp(1) has mean 1, var 1
+    assert np.allclose(O.block_medians(A[1024:], 1024), math.log(2.0), rtol=1e-12)
+    assert abs(P.mean() - 1.0) < 0.02 and abs(P.var() - 1.0) < 0.06
+    assert abs(np.mean(P > 3.0) - math.exp(-3.0)) < 0.005
+
+
+# ---------------------------------------------------------------- correlation
+def test_correlate_z0_is_identity():
+    A = synth.random_spectrum(500, 3).astype(np.complex128)
+    F = O.correlate(A, [0.0])
+    assert np.abs(F[0] - A).max() < 1e-14
+
+
+def test_correlate_matches_python_loops():
+    A = synth.random_spectrum(40, 4).astype(np.complex128)
+    zs = [-6.0, 0.0, 4.0]
+    F = O.correlate(A, zs)
+    for k, z in enumerate(zs):
+        h = O.half_width(z)
+        for r in range(40):
+            acc = 0j
+            for d in range(-h, h + 1):
+                if 0 <= r + d < 40:
+                    acc += A[r + d] * np.conj(O.template_response(z, d))
+            assert abs(F[k, r] - acc) < 1e-12
+
+
+def test_correlate_equals_overlap_save():
+    """Overlap-save with numpy FFTs (Section 3, Fig. 1) gives the tap sum."""
+    nb, L, M = 3000, 256, 64
+    B = L - M
+    A = synth.random_spectrum(nb, 5).astype(np.complex128)
+    zs = [-20.0, -6.0, 0.0, 14.0, 20.0]
+    F = O.correlate(A, zs)
+    padded = np.concatenate([np.zeros(M // 2), A, np.zeros(L)])
+    for k, z in enumerate(zs):
+        H = O.kernel_spectrum(z, L)
+        out = []
+        for s in range((nb + B - 1) // B):
+            blk = padded[s * B: s * B + L]
+            y = np.fft.ifft(np.fft.fft(blk) * H) * L
+            out.append(y[M // 2: M // 2 + B])
+        osv = np.concatenate(out)[:nb]
+        assert np.abs(osv - F[k]).max() < 1e-10
+
+
+def test_correlate_matched_template_peaks_at_truth():
+    # A spectrum equal to a template (shifted to r0) correlates to sum |R|^2 at
+    # (r0, z0) and, by Cauchy-Schwarz, to less anywhere else.
+    nb, r0 = 2000, 900
+    zs = O.z_grid(-20, 20, 2)
+    for z0 in (-14.0, 0.0, 8.0):
+        d = np.arange(-400, 401)
+        A = np.zeros(nb, np.complex128)
+        A[r0 + d] = O.template_response(z0, d)
+        F = O.correlate(A, zs)
+        k0 = int(np.where(zs == z0)[0][0])
+        h = O.half_width(z0)
+        e = np.sum(np.abs(O.template_response(z0, np.arange(-h, h + 1))) ** 2)
+        assert abs(F[k0, r0] - e) < 1e-12
+        P = np.abs(F) ** 2
+        assert np.unravel_index(np.argmax(P), P.shape) == (k0, r0)
+
+
+# ---------------------------------------------------------------- interbinning
+def _tone(nb, r0):
+    # continuous-limit spectrum of a unit tone at fractional bin r0: R_0(k - r0)
+    return O.template_response(0.0, np.arange(nb) - r0)
+
+
+def test_interbin_half_and_integer_tones():
+    nb = 64
+    P = O.power_plane(O.correlate(_tone(nb, 20.5), [0.0]))
+    assert abs(P[0, 2 * 20 + 1] - 1.0) < 1e-12            # half bin recovers full amplitude
+    assert abs(P[0, 2 * 20] - (2 / math.pi) ** 2) < 1e-12   # sinc(1/2)^2 at the full bin
+    P = O.power_plane(O.correlate(_tone(nb, 20.0), [0.0]))
+    assert abs(P[0, 40] - 1.0) < 1e-12 and abs(P[0, 41] - (math.pi / 4) ** 2) < 1e-12
+    assert P[0, -1] == 0.0
+
+
+def test_interbin_worst_case_loss_matches_paper():
+    g = json.load(open(os.path.join(GOLDEN, "interbin_loss.json")))
+    nb = 64
+    best_ib, best_full = [], []
+    for f in np.linspace(0.0, 1.0, 201):
+        P = O.power_plane(O.correlate(_tone(nb, 20.0 + f), [0.0]))[0, 36:48]
+        best_ib.append(math.sqrt(P.max()))
+        best_full.append(math.sqrt(P[0::2].max()))
+    loss_ib = 1 - min(best_ib)
+    loss_full = 1 - min(best_full)
+    assert abs(loss_ib - g["max_amplitude_loss_interbinned"]) < g["tolerance"]
+    assert abs(loss_full - g["max_amplitude_loss_full_bins_only"]) < g["tolerance"]
+
+
+def test_plane_window_and_points_agree_with_full_plane():
+    A = synth.random_spectrum(700, 6).astype(np.complex128)
+    zs = O.z_grid(-10, 10, 2)
+    P = O.plane(A, zs)
+    assert np.allclose(O.plane_window(A, zs, 100, 50), P[:, 200:300], atol=1e-13, rtol=0)
+    assert np.allclose(O.plane_window(A, zs, 650, 50), P[:, 1300:1400], atol=1e-13, rtol=0)
+    zi = np.array([0, 3, 10, 10, 5])
+    col = np.array([0, 77, 1399, 1398, 640])
+    assert np.allclose(O.plane_points(A, zs, zi, col), P[zi, col], atol=1e-13, rtol=0)
+    assert np.allclose(O.plane(A, zs, interbin=False), P[:, 0::2], atol=1e-13, rtol=0)
+
+
+# ---------------------------------------------------------------- candidates
+def test_threshold_and_peak_ties():
+    P = np.zeros((3, 6))
+    P[1, 2] = 30.0
+    P[1, 3] = 30.0     # tie with the earlier neighbour -> (1,2) is the peak
+    P[0, 0] = 25.0
+    P[2, 5] = 19.0
+    P[2, 4] = 21.0
+    rows, cols, pw, fl = O.threshold(P, 20.0)
+    assert list(zip(rows, cols)) == [(0, 0), (1, 2), (1, 3), (2, 4)]
+    assert list(fl) == [1, 1, 0, 0]          # (2,4) is below its neighbour (1,3)
+    assert np.all(pw > 20.0)
+    rows, cols, pw, fl = O.threshold(np.full((2, 2), 20.0), 20.0)
+    assert len(rows) == 0                     # strict P > T
+
+
+def test_injection_recovered_on_grid():
+    """An on-grid chirp peaks exactly at its (r0, z0), power ~ SNR^2 sum|R|^2."""
+    n, r0, z0, snr = 1 << 14, 3000.0, 8.0, 30.0
+    x = synth.make_series(n, ((r0, z0, snr),), seed=21)
+    A, P, (rows, cols, pw, fl) = O.search(x, -20, 20, 2, 1024, 20.0)
+    k, c = np.unravel_index(np.argmax(P), P.shape)
+    assert O.z_grid(-20, 20, 2)[k] == z0 and c == 2 * int(r0)
+    h = O.half_width(z0)
+    e = np.sum(np.abs(O.template_response(z0, np.arange(-h, h + 1))) ** 2)
+    assert abs(P[k, c] / (snr ** 2 * e) - 1.0) < 0.15
+    assert np.any((rows == k) & (cols == c) & (fl == O.PEAK_FLAG))
+
+
+def test_injection_recovered_off_grid_within_paper_tolerance():
+    """Off-grid truths are found within +-1/2 bin and +-1 z step (Section 5.2)."""
+    wl = synth.workload("tiny")
+    A, P, _ = O.search(wl.series(), wl.zmin, wl.zmax, wl.zstep, wl.median_block, wl.threshold)
+    zs = O.z_grid(wl.zmin, wl.zmax, wl.zstep)
+    for r0, z0, snr in wl.injections:
+        lo, hi = int(2 * (r0 - 8)), int(2 * (r0 + 8))
+        sub = P[:, lo:hi]
+        k, c = np.unravel_index(np.argmax(sub), sub.shape)
+        assert abs((lo + c) / 2.0 - r0) <= 0.5 + 1e-9
+        assert abs(zs[k] - z0) <= wl.zstep
