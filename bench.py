@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""FDAS correlation benchmark: f-fdot plane points/s for a 2^23-sample series.
+
+One step = the whole hot path on one synthetic series already resident in
+HBM: template bank (fdas_make_templates), real FFT + running-median
+normalisation (fdas_normalise), and the fused overlap-save convolver with the
+threshold in its epilogue (fdas_correlate), writing the 201 x 2^23 FP32
+plane.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--L 2048] [--workload production]
+
+Under torchrun each rank searches its own series (independent dispersion
+trials: replicas, no collective on the data path); the timed region is
+bracketed by a barrier and synchronisation and the time is the max over
+ranks.  --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "f-fdot plane points/s (2^23-sample series, zmax=200)"
+UNIT = "points/s"
+KERNELS_PER_STEP = 6   # templates 1, normalise 4, convolver 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="production")
+    ap.add_argument("--L", type=int, default=0, help="segment length (default: workload's)")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cap", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    wl = synth.workload(args.workload)
+    if args.L:
+        wl = wl.with_(L=args.L)
+    return wl
+
+
+def describe(wl):
+    return ("%s: %d-sample series (%d bins), %d templates z=%d..%d step %d, M=%d taps, "
+            "L=%d segments, interbinned FP32 plane %dx%d, threshold %g"
+            % (wl.name, wl.n, wl.nb, wl.K, wl.zmin, wl.zmax, wl.zstep, wl.M, wl.L, wl.K,
+               2 * wl.nb, wl.threshold))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def conv_source_sha():
+    h = hashlib.sha256()
+    for f in ("convolve.cu", "dft.cuh"):
+        with open(os.path.join(ROOT, "paper_1804_05335_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel_key)
+        if rec and rec.get("source_sha") == conv_source_sha():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:  # noqa: BLE001
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="fdas_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append((float(f[2]), float(f[3]), f[6:10]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+def oracle_rate(wl, x, seconds, rng_seed=0):
+    """Oracle plane points/s on a bounded sample of the workload (host cores)."""
+    import oracle.fdas_oracle as O
+    t0 = time.perf_counter()
+    A = O.normalise(O.real_spectrum(x), wl.median_block)
+    t_fe = time.perf_counter() - t0
+    zs = O.z_grid(wl.zmin, wl.zmax, wl.zstep)
+    O.correlate(A, zs, 1000, 64)            # loads the library, warms the caches
+    nr = 2048
+    t0 = time.perf_counter()
+    O.plane_window(A, zs, wl.nb // 3, nr)
+    t1 = time.perf_counter() - t0
+    nr = int(min(wl.nb - 1, max(nr, nr * seconds / max(t1, 1e-3))))
+    start = int(np.random.default_rng(rng_seed).integers(0, wl.nb - nr))
+    t0 = time.perf_counter()
+    O.plane_window(A, zs, start, nr)
+    t_corr = time.perf_counter() - t0
+    t_total = t_corr + t_fe * nr / wl.nb
+    pts = wl.K * 2 * nr
+    return pts / t_total, {
+        "cores": O.oracle_threads(),
+        "sample": ("FP64 oracle: real FFT + median normalisation of the whole %d-sample series "
+                   "(%.2f s, charged pro rata) and the direct tap-sum plane for all %d templates "
+                   "over %d of %d bins (%.2f s)" % (wl.n, t_fe, wl.K, nr, wl.nb, t_corr)),
+    }
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    wl = workload(args)
+    import oracle.fdas_oracle as O
+    x = wl.series()
+    t0 = time.perf_counter()
+    A = O.normalise(O.real_spectrum(x), wl.median_block)
+    t_fe = time.perf_counter() - t0
+    zs = O.z_grid(wl.zmin, wl.zmax, wl.zstep)
+    nr = 512
+    rng = np.random.default_rng(0)
+    for _ in range(max(args.warmup, 0)):
+        O.plane_window(A, zs, int(rng.integers(0, wl.nb - nr)), nr)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.plane_window(A, zs, int(rng.integers(0, wl.nb - nr)), nr)
+    t_corr = time.perf_counter() - t0
+    t = t_corr + args.steps * t_fe * nr / wl.nb
+    pts = wl.K * 2 * nr * args.steps
+    value = pts / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": describe(wl), "sample_bins_per_step": nr},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.oracle_threads(),
+                         "kind": "oracle",
+                         "sample": "each step: all %d templates over %d random bins, plus the "
+                                   "front end charged pro rata" % (wl.K, nr)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native leg
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_05335_gb300.search import Search
+
+    wl = workload(args)
+    x = synth.make_series(wl.n, wl.injections, wl.seed + rank)
+    S = Search(wl.n, wl.L, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
+               median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
+    host_series = torch.from_numpy(x).pin_memory()
+    S.series.copy_(host_series)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    points = S.K * S.width
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        S.step()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = vis.split(",")[local] if vis else str(local)
+    sampler = ClockSampler(phys)
+    time.sleep(0.3)
+    # keep the GPU busy a moment so the clocks seen are the loaded ones
+    for _ in range(max(5, args.warmup // 2)):
+        S.step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                     # 256 MiB write evicts L2 between steps
+        e0, e1, e2 = evs[i]
+        e0.record()
+        S.make_templates()
+        S.normalise()
+        e1.record()
+        S.correlate(True)
+        e2.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, _, c in evs]
+    conv_ms = [b.elapsed_time(c) for _, b, c in evs]
+    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    total_ms = float(total.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * points * args.steps / (total_ms / 1e3)
+
+    # end to end: host series -> device, the step, candidates -> host
+    cand_host = torch.empty(1 + 4 * S.cap, dtype=torch.int32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.e2e_steps):
+        S.series.copy_(host_series, non_blocking=True)
+        S.step()
+        cand_host[:1].copy_(S.count, non_blocking=True)
+        cand_host[1:].copy_(S.cand, non_blocking=True)
+    s1.record()
+    torch.cuda.synchronize()
+    e2e_t = torch.tensor([s0.elapsed_time(s1)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * points * args.e2e_steps / (float(e2e_t.item()) / 1e3)
+    n_cand = int(cand_host[0].item())
+
+    if rank == 0:
+        peak, peak_kind = measured_peak()
+        conv_mean = statistics.mean(conv_ms)
+        alg_bytes = S.K * S.width * 4 + S.nb * 8 + S.Kb * S.L * 8
+        achieved = alg_bytes / (conv_mean / 1e3) / 1e9
+        key = "conv_kernel<%d,true>" % wl.L
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(wl), "n": wl.n, "nb": wl.nb, "K": S.K, "L": wl.L,
+                       "M": wl.M, "segments": S.nseg, "plane_points": points,
+                       "plane_bytes": points * 4, "per_rank": "independent series per rank",
+                       "l2": "flushed between timed steps (256 MiB write); plane 6.7 GB > L2"},
+            "roofline": {"bound": "hbm", "kernel": key, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": recorded_traffic(key),
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                         if peak_kind == "measured" else "fallback 6800 GB/s",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel_ms": conv_mean},
+            "front_ms": statistics.mean(a - b for a, b in zip(step_ms, conv_ms)),
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": wl.n * 4, "d2h_bytes_per_step": 4 * (1 + 4 * S.cap),
+                    "candidates": n_cand},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clocks,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            v, info = oracle_rate(wl, x, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"],
+                                    "kind": "oracle", "sample": info["sample"]}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * fdas.h -- C ABI of the GB300 (sm_103a) FDAS correlation library.
+ *
+ * Fourier Domain Acceleration Search by the correlation technique: a
+ * normalised complex spectrum is correlated with a bank of acceleration
+ * templates, one per trial frequency derivative z, by overlap-save (segment
+ * FFT -> pointwise multiply per template -> inverse FFT -> discard the
+ * contaminated edges -> power at full and half bins), giving the f-fdot power
+ * plane, which is then thresholded for candidates (Sections 2-4).
+ *
+ * Conventions for every call:
+ *  - Pointers marked (device) are CUDA device pointers owned by the caller;
+ *    the library allocates no device memory.  Pointers marked (host) are
+ *    ordinary host memory.
+ *  - Complex values are interleaved float pairs (re, im); a "complex" array
+ *    of length n is float[2n], 8-byte aligned (16-byte where stated).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    compute call is asynchronous on that stream and returns before the GPU
+ *    work finishes.
+ *  - Return value: FDAS_OK (0) or a negative FDAS_E_* code.  Arguments are
+ *    validated before anything is launched; on FDAS_E_INVAL nothing was
+ *    launched.  FDAS_E_CUDA reports a launch error of this call.
+ *  - Conditions found on the device (candidate overflow) are OR-ed as
+ *    FDAS_STATUS_* bits into a caller-owned device int32 status word, which
+ *    the caller zeroes and reads back after synchronising.
+ *  - Calls may run concurrently on different streams if their output
+ *    buffers do not overlap.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDAS_OK 0
+#define FDAS_E_INVAL (-1)       /* bad argument; nothing launched */
+#define FDAS_E_CUDA (-2)        /* a CUDA launch or runtime error */
+#define FDAS_E_OVERFLOW (-3)    /* candidate buffer too small (see status word) */
+#define FDAS_E_TIMEOUT (-4)     /* a bounded device wait gave up (see status word) */
+#define FDAS_E_UNSUPPORTED (-5) /* valid but unsupported size or device */
+
+#define FDAS_STATUS_TIMEOUT 1   /* status-word bit: a device wait gave up */
+#define FDAS_STATUS_OVERFLOW 2  /* status-word bit: more candidates than `cap` */
+
+#define FDAS_CAND_PEAK 1        /* fdas_cand.flags bit: local maximum (8 neighbours) */
+
+/* Search parameters.
+ *  L        overlap-save segment (FFT) length: 1024, 2048 or 4096 (Section 3,
+ *           Fig. 1: blocks of L = B + M points).
+ *  M        padded template width in taps: a multiple of 4 with
+ *           64 <= M <= L/2; each segment yields B = L - M useful bins and
+ *           the longest template must fit: h(max|z|) <= M/2 - 1.
+ *  zmin, zmax, zstep
+ *           template grid z_j = zmin + j*zstep, j = 0..K-1,
+ *           K = (zmax - zmin)/zstep + 1; zstep >= 1, (zmax - zmin) % zstep == 0.
+ *           If zmin == -zmax the grid is symmetric and the bank stores only
+ *           the z >= 0 templates: a z < 0 template is applied as the
+ *           complex conjugate of its +|z| partner with reversed frequency
+ *           index (Section 4.2).
+ *  interbin 1: plane rows hold 2*nb columns, column 2r = |F_r|^2 and
+ *           column 2r+1 = (pi/4)^2 |F_r - F_{r+1}|^2 (Eq. f-interp), the last
+ *           one 0;  0: rows hold nb columns |F_r|^2.
+ * The template half-width is h(z) = ceil(|z|/2) + 8 taps. */
+typedef struct {
+    int32_t L;
+    int32_t M;
+    int32_t zmin;
+    int32_t zmax;
+    int32_t zstep;
+    int32_t interbin;
+} fdas_params;
+
+/* One threshold crossing: plane row (z index), column (2r or 2r+1 with
+ * interbinning, r without), power, FDAS_CAND_* flags. */
+typedef struct {
+    int32_t z_idx;
+    int32_t col;
+    float power;
+    int32_t flags;
+} fdas_cand;
+
+/* Threshold applied inside fdas_correlate's epilogue (flags are 0: no peak
+ * test).  `count` (device) is reset to 0 by the call and ends holding the
+ * number of crossings found, which may exceed `cap`; only the first `cap`
+ * are stored, in no particular order, and FDAS_STATUS_OVERFLOW is set. */
+typedef struct {
+    float thr;          /* strict: power > thr */
+    fdas_cand *out;     /* (device) cap entries */
+    int32_t cap;
+    int32_t *count;     /* (device) one int32 */
+} fdas_fused_threshold;
+
+/* Message for an FDAS_* return code (static string). */
+const char *fdas_strerror(int code);
+
+/* Library version as "major.minor.patch" (static string). */
+const char *fdas_version(void);
+
+/* Template half-width h(z) = ceil(|z|/2) + 8 taps. */
+int32_t fdas_half_width(int32_t z);
+
+/* Number of templates K of the grid (< 0: FDAS_E_INVAL). */
+int32_t fdas_num_templates(const fdas_params *p);
+
+/* Number of bank rows K' (K, or (K+1)/2-ish for a symmetric grid; < 0 on
+ * error).  Bank row b holds template z = zmin + (b + j0)*zstep, where j0 is
+ * the number of negative z in a symmetric grid and 0 otherwise. */
+int32_t fdas_bank_rows(const fdas_params *p);
+
+/* Number of overlap-save segments for nb bins: ceil(nb / (L - M)). */
+int64_t fdas_num_segments(const fdas_params *p, int64_t nb);
+
+/* Plane row width in floats for nb bins (2*nb with interbinning, else nb). */
+int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
+
+/*
+ * fdas_make_templates -- build the frequency-domain template bank
+ * (a1: Section 2 Eq. 23; Section 3 Fig. 1 and the zero-filled centring of
+ * the L-point filter; Section 4.2 +/-z symmetry).
+ *
+ * For bank row b with template z, the response is
+ *   R_z(d) = int_0^1 exp(i 2 pi (z u^2/2 - (d + z/2) u)) du   (FP64, Fresnel)
+ * for d = -h..h, the FIR kernel g[j] = conj(R_z(-j)) is placed circularly
+ * (j >= 0 at the start, j < 0 at the end, zeros between) and
+ *   H_z[k] = (1/L) sum_j g[j] exp(-i 2 pi j k / L),  k = 0..L-1
+ * is stored in FP32 in the convolver's digit-reversed order:
+ *   bank[(b*L + s)*2 + {0,1}] = H_z[k(s)] (re, im), slot s = 0..L-1,
+ *   with Q = L/256, T = L/16, s = 2*(ip*T + t) + e, i = 2*ip + e,
+ *   t = a*Q + c1, i = s2*Q + c2  ->  k(s) = a + 16*(c1 + Q*s2) + 256*c2.
+ * bank: (device) fdas_bank_rows(p) * L complex, 16-byte aligned; written.
+ * Errors: FDAS_E_INVAL for bad params or NULL bank.
+ */
+int fdas_make_templates(const fdas_params *p, float *bank, void *stream);
+
+/* Workspace bytes fdas_normalise needs for n samples (0 if n unsupported). */
+size_t fdas_normalise_workspace_bytes(int64_t n);
+
+/*
+ * fdas_normalise -- real FFT of the series and running-median
+ * normalisation (a2-a3: Section 3 first paragraph on the workflow, Section
+ * 4.1 real-to-complex transform, DFT sign of Section 4.2).
+ *   X_k = sum_t series[t] exp(-i 2 pi k t / n),  k = 0..n/2-1,  X_0 := 0
+ *   (the Nyquist bin is dropped);  for each block of `median_block`
+ *   consecutive bins (the last block takes the remainder), m = the lower
+ *   median (rank floor((len-1)/2)) of |X_k|^2 in the block, and
+ *   spec_k = X_k / sqrt(m / ln 2)  (0 if m == 0), so noise power has mean 1.
+ * series: (device) n floats, 8-byte aligned.  n: power of two,
+ *   2^13 <= n <= 2^25.  median_block: 32..8192.
+ * spec: (device) n/2 complex, written.
+ * work: (device) fdas_normalise_workspace_bytes(n) bytes, 16-byte aligned;
+ *   scratch, contents undefined afterwards.
+ * Errors: FDAS_E_INVAL (NULL pointers, unsupported n or block, work_bytes
+ *   too small).
+ */
+int fdas_normalise(const float *series, int64_t n, int32_t median_block, float *spec,
+                   void *work, size_t work_bytes, void *stream);
+
+/*
+ * fdas_correlate -- the fused overlap-save convolver (a4-a7: Section 3
+ * Fig. 1 and the text after it; Section 4.1 Fig. 3; Section 4.2 fused
+ * on-chip FFT/multiply/inverse-FFT/power; Eq. f-interp).
+ * For every template row j (z_j) and bin r = 0..nb-1:
+ *   F_j(r) = sum_{d=-h}^{h} spec[r + d] conj(R_{z_j}(d))   (spec = 0 outside [0,nb)),
+ * computed by segments s = 0..S-1 of L bins starting at bin s*B - M/2
+ * (B = L - M), one forward FFT per segment, one multiply + inverse FFT per
+ * (segment, template), keeping positions M/2..M/2+B of each inverse FFT.
+ * plane[j*row_stride + c] then holds the power plane (interbin layout in
+ * fdas_params); the plane is written once, no other global memory is used.
+ * spec: (device) nb complex.  bank: (device) as made by fdas_make_templates
+ *   for the same p, 16-byte aligned.  plane: (device) K rows of row_stride
+ *   floats, 16-byte aligned, row_stride >= fdas_plane_width and a multiple
+ *   of 4.  nb >= 1.
+ * fused: NULL, or a threshold applied to every plane value as it is written.
+ * status: (device) int32 word for FDAS_STATUS_* bits, or NULL.
+ * Errors: FDAS_E_INVAL (bad params, alignment, NULL pointers).
+ */
+int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const float *bank,
+                   float *plane, int64_t row_stride, const fdas_fused_threshold *fused,
+                   int32_t *status, void *stream);
+
+/*
+ * fdas_threshold -- candidates of a power plane (a8: Section 3, comparing
+ * the Fourier power with a pre-computed threshold).
+ * Emits every (row, col) with plane value > thr (strict).  With
+ * FDAS_CAND_PEAK in `want_flags`, flags gets FDAS_CAND_PEAK where the value
+ * is a local maximum of its 8 neighbours (strictly above neighbours earlier
+ * in row-major order, at least equal to later ones).
+ * plane: (device) rows x width floats, row stride row_stride >= width.
+ * out: (device) cap entries, unordered.  count: (device) reset to 0 by the
+ * call, ends holding the total number of crossings (may exceed cap).
+ * status: (device) FDAS_STATUS_OVERFLOW is OR-ed in when count > cap; may be
+ * NULL.  Errors: FDAS_E_INVAL.
+ */
+int fdas_threshold(const float *plane, int32_t rows, int64_t width, int64_t row_stride,
+                   float thr, int32_t want_flags, fdas_cand *out, int32_t cap,
+                   int32_t *count, int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

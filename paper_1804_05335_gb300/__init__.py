@@ -1,0 +1,200 @@
+"""Python binding of libfdas, the sm_103a FDAS correlation library.
+
+The functions here carry the C ABI's names (include/fdas.h) and only marshal
+arguments: torch tensors supply device memory and the current CUDA stream,
+and every step of the search runs in the library's kernels.  There is no CPU
+fallback: if libfdas.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+__all__ = [
+    "FdasError", "fdas_params", "fdas_cand", "fdas_fused_threshold", "load_library", "lib_path",
+    "params", "fdas_strerror", "fdas_version", "fdas_half_width", "fdas_num_templates",
+    "fdas_bank_rows", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
+    "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_correlate", "fdas_threshold",
+    "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
+    "FDAS_OK", "FDAS_E_INVAL", "FDAS_E_CUDA", "FDAS_E_OVERFLOW", "FDAS_E_TIMEOUT",
+    "FDAS_E_UNSUPPORTED",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libfdas.so")
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "fdas.h")
+
+FDAS_OK = 0
+FDAS_E_INVAL = -1
+FDAS_E_CUDA = -2
+FDAS_E_OVERFLOW = -3
+FDAS_E_TIMEOUT = -4
+FDAS_E_UNSUPPORTED = -5
+FDAS_STATUS_TIMEOUT = 1
+FDAS_STATUS_OVERFLOW = 2
+FDAS_CAND_PEAK = 1
+
+c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+
+class fdas_params(ctypes.Structure):
+    _fields_ = [("L", c_i32), ("M", c_i32), ("zmin", c_i32), ("zmax", c_i32),
+                ("zstep", c_i32), ("interbin", c_i32)]
+
+
+class fdas_cand(ctypes.Structure):
+    _fields_ = [("z_idx", c_i32), ("col", c_i32), ("power", c_f32), ("flags", c_i32)]
+
+
+class fdas_fused_threshold(ctypes.Structure):
+    _fields_ = [("thr", c_f32), ("out", c_vp), ("cap", c_i32), ("count", c_vp)]
+
+
+class FdasError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, _strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libfdas.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libfdas.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "fdas_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "fdas_version": (ctypes.c_char_p, []),
+        "fdas_half_width": (c_i32, [c_i32]),
+        "fdas_num_templates": (c_i32, [P(fdas_params)]),
+        "fdas_bank_rows": (c_i32, [P(fdas_params)]),
+        "fdas_num_segments": (c_i64, [P(fdas_params), c_i64]),
+        "fdas_plane_width": (c_i64, [P(fdas_params), c_i64]),
+        "fdas_make_templates": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
+        "fdas_normalise_workspace_bytes": (c_sz, [c_i64]),
+        "fdas_normalise": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]),
+        "fdas_correlate": (ctypes.c_int, [P(fdas_params), c_vp, c_i64, c_vp, c_vp, c_i64,
+                                          P(fdas_fused_threshold), c_vp, c_vp]),
+        "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
+                                          c_vp, c_vp, c_vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions():
+    """Names of the functions declared in include/fdas.h."""
+    txt = open(_HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdas_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load_library().fdas_strerror(int(code)).decode()
+    except Exception:  # noqa: BLE001 - only used while formatting an error
+        return "error"
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise FdasError(int(rc), what)
+    return rc
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def params(L=2048, M=256, zmin=-200, zmax=200, zstep=2, interbin=1) -> fdas_params:
+    return fdas_params(int(L), int(M), int(zmin), int(zmax), int(zstep), int(interbin))
+
+
+def fdas_strerror(code: int) -> str:
+    return load_library().fdas_strerror(int(code)).decode()
+
+
+def fdas_version() -> str:
+    return load_library().fdas_version().decode()
+
+
+def fdas_half_width(z: int) -> int:
+    return int(load_library().fdas_half_width(int(z)))
+
+
+def fdas_num_templates(p: fdas_params) -> int:
+    return _check(load_library().fdas_num_templates(ctypes.byref(p)), "fdas_num_templates")
+
+
+def fdas_bank_rows(p: fdas_params) -> int:
+    return _check(load_library().fdas_bank_rows(ctypes.byref(p)), "fdas_bank_rows")
+
+
+def fdas_num_segments(p: fdas_params, nb: int) -> int:
+    return _check(load_library().fdas_num_segments(ctypes.byref(p), int(nb)), "fdas_num_segments")
+
+
+def fdas_plane_width(p: fdas_params, nb: int) -> int:
+    return _check(load_library().fdas_plane_width(ctypes.byref(p), int(nb)), "fdas_plane_width")
+
+
+def fdas_make_templates(p: fdas_params, bank, stream=None) -> None:
+    """bank: device float32 tensor of fdas_bank_rows(p) * L * 2 elements."""
+    _check(load_library().fdas_make_templates(ctypes.byref(p), _ptr(bank), _stream(stream)),
+           "fdas_make_templates")
+
+
+def fdas_normalise_workspace_bytes(n: int) -> int:
+    return int(load_library().fdas_normalise_workspace_bytes(int(n)))
+
+
+def fdas_normalise(series, n: int, median_block: int, spec, work, work_bytes: int,
+                   stream=None) -> None:
+    """series: device float32[n]; spec: device complex64[n/2] (or float32[n])."""
+    _check(load_library().fdas_normalise(_ptr(series), int(n), int(median_block), _ptr(spec),
+                                         _ptr(work), int(work_bytes), _stream(stream)),
+           "fdas_normalise")
+
+
+def fdas_correlate(p: fdas_params, spec, nb: int, bank, plane, row_stride: int,
+                   fused: fdas_fused_threshold | None = None, status=None, stream=None) -> None:
+    f = ctypes.byref(fused) if fused is not None else None
+    _check(load_library().fdas_correlate(ctypes.byref(p), _ptr(spec), int(nb), _ptr(bank),
+                                         _ptr(plane), int(row_stride), f, _ptr(status),
+                                         _stream(stream)), "fdas_correlate")
+
+
+def fdas_threshold(plane, rows: int, width: int, row_stride: int, thr: float, want_flags: int,
+                   out, cap: int, count, status=None, stream=None) -> None:
+    _check(load_library().fdas_threshold(_ptr(plane), int(rows), int(width), int(row_stride),
+                                         float(thr), int(want_flags), _ptr(out), int(cap),
+                                         _ptr(count), _ptr(status), _stream(stream)),
+           "fdas_threshold")

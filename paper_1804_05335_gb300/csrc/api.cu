@@ -1,0 +1,116 @@
+// Argument validation, grid bookkeeping and the small C-ABI helpers.
+#include <stdlib.h>
+
+#include "internal.h"
+
+namespace fdas {
+
+static int32_t half_width_i(int32_t z) {
+    int32_t az = z < 0 ? -z : z;
+    return (az + 1) / 2 + 8;   // ceil(|z|/2) + 8
+}
+
+int make_grid(const fdas_params* p, Grid* g) {
+    if (!p || !g) return FDAS_E_INVAL;
+    if (p->L != 1024 && p->L != 2048 && p->L != 4096) return FDAS_E_INVAL;
+    if (p->M < 64 || p->M > p->L / 2 || (p->M % 4) != 0) return FDAS_E_INVAL;
+    if (p->zstep < 1 || p->zmin > p->zmax) return FDAS_E_INVAL;
+    if ((int64_t)p->zmax - (int64_t)p->zmin > 100000) return FDAS_E_INVAL;
+    if ((p->zmax - p->zmin) % p->zstep != 0) return FDAS_E_INVAL;
+    if (p->interbin != 0 && p->interbin != 1) return FDAS_E_INVAL;
+    int32_t zabs = abs(p->zmin) > abs(p->zmax) ? abs(p->zmin) : abs(p->zmax);
+    int32_t hmax = half_width_i(zabs);
+    if (hmax > p->M / 2 - 1) return FDAS_E_INVAL;   // template must fit the discarded edge
+    g->K = (p->zmax - p->zmin) / p->zstep + 1;
+    g->hmax = hmax;
+    g->sym = (p->zmin == -p->zmax && p->zmax > 0) ? 1 : 0;
+    if (g->sym) {
+        int32_t j0 = 0;
+        while (j0 < g->K && p->zmin + j0 * p->zstep < 0) ++j0;
+        g->j0 = j0;
+        g->Kb = g->K - j0;
+        g->zero = (p->zmin + j0 * p->zstep == 0) ? 1 : 0;
+    } else {
+        g->j0 = 0;
+        g->Kb = g->K;
+        g->zero = 0;
+    }
+    return FDAS_OK;
+}
+
+}  // namespace fdas
+
+using namespace fdas;
+
+extern "C" {
+
+const char* fdas_strerror(int code) {
+    switch (code) {
+        case FDAS_OK: return "ok";
+        case FDAS_E_INVAL: return "invalid argument";
+        case FDAS_E_CUDA: return "CUDA error";
+        case FDAS_E_OVERFLOW: return "candidate buffer overflow";
+        case FDAS_E_TIMEOUT: return "device wait timed out";
+        case FDAS_E_UNSUPPORTED: return "unsupported size or device";
+        default: return "unknown error";
+    }
+}
+
+const char* fdas_version(void) { return "0.1.0"; }
+
+int32_t fdas_half_width(int32_t z) { return half_width_i(z); }
+
+int32_t fdas_num_templates(const fdas_params* p) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    return rc == FDAS_OK ? g.K : rc;
+}
+
+int32_t fdas_bank_rows(const fdas_params* p) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    return rc == FDAS_OK ? g.Kb : rc;
+}
+
+int64_t fdas_num_segments(const fdas_params* p, int64_t nb) {
+    Grid g;
+    if (make_grid(p, &g) != FDAS_OK || nb < 1) return FDAS_E_INVAL;
+    int64_t B = p->L - p->M;
+    return (nb + B - 1) / B;
+}
+
+int64_t fdas_plane_width(const fdas_params* p, int64_t nb) {
+    Grid g;
+    if (make_grid(p, &g) != FDAS_OK || nb < 1) return FDAS_E_INVAL;
+    return p->interbin ? 2 * nb : nb;
+}
+
+int fdas_make_templates(const fdas_params* p, float* bank, void* stream) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    if (!bank || !aligned(bank, 16)) return FDAS_E_INVAL;
+    return launch_templates(p, g, reinterpret_cast<float2*>(bank), (cudaStream_t)stream);
+}
+
+int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const float* bank,
+                   float* plane, int64_t row_stride, const fdas_fused_threshold* fused,
+                   int32_t* status, void* stream) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    if (!spec || !bank || !plane || nb < 1 || nb > ((int64_t)1 << 31)) return FDAS_E_INVAL;
+    if (!aligned(spec, 8) || !aligned(bank, 16) || !aligned(plane, 16)) return FDAS_E_INVAL;
+    int64_t width = p->interbin ? 2 * nb : nb;
+    if (row_stride < width || (row_stride % 4) != 0) return FDAS_E_INVAL;
+    if (fused) {
+        if (!fused->out || !fused->count || fused->cap < 0) return FDAS_E_INVAL;
+        if (!aligned(fused->out, 4) || !aligned(fused->count, 4)) return FDAS_E_INVAL;
+    }
+    if (status && !aligned(status, 4)) return FDAS_E_INVAL;
+    return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
+                            reinterpret_cast<const float4*>(bank), plane, row_stride, fused,
+                            status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,360 @@
+// fdas_correlate: fused overlap-save convolver (Sections 3, 4.1, 4.2).
+//
+// One persistent CTA per SM slot walks a contiguous, statically balanced
+// range of (segment, template) work items in segment-major order.  For each
+// new segment it loads the L spectrum bins starting at s*B - M/2 (zero
+// outside [0, nb)) and runs the forward FFT once; for every template it
+// multiplies by the template spectrum, runs the inverse FFT, forms full- and
+// half-bin powers of the B useful outputs and writes them to the plane with
+// 16-byte coalesced stores.  Nothing but the plane (and optional candidates)
+// is written to global memory.
+//
+// FFT layout (L = 16*16*Q, T = L/16 threads, 16 complex values per thread):
+// the forward transform is decimation-in-frequency in three register passes
+// (radix 16, 16, Q) separated by shared-memory exchanges, and leaves the
+// spectrum digit-reversed; the inverse is the transposed decimation-in-time
+// sequence (radix Q, 16, 16), which takes digit-reversed input and returns
+// natural order.  The pointwise product therefore never needs the reordering
+// permutation (Section 4.2), and the template bank is stored in the same
+// digit-reversed order.  Thread/register distributions (p = position):
+//   D1: thread t, reg i          p = i*T + t
+//   D2: thread t = a*Q + c, reg b  p = a*T + b*Q + c
+//   D3: thread t = a*Q + c, reg i = s*Q + c2   p = a*T + (c + Q*s)*Q + c2
+// D2 <-> D3 exchanges stay inside a group of Q threads (one warp), D1 <-> D2
+// needs the whole CTA.  Both shared-memory layouts are padded so that every
+// exchange is free of bank conflicts.
+//
+// z < 0 templates of a symmetric grid use H_{-z}[k] = conj(H_z[-k mod L])
+// (Section 4.2): in D3, -k of (thread t, reg i) lives in (partner(t), 15-i)
+// except for thread 0, handled separately.
+#include <algorithm>
+
+#include "dft.cuh"
+#include "internal.h"
+
+namespace fdas {
+
+struct ConvArgs {
+    const float2* spec;
+    int64_t nb;
+    const float4* bank;
+    float* plane;
+    int64_t row_stride;
+    int64_t items;      // nseg * K
+    int32_t K;
+    int32_t j0;
+    int32_t sym;
+    int32_t zero;
+    int32_t M;
+    int32_t interbin;
+    float thr;
+    fdas_cand* cand;
+    int32_t cap;
+    int32_t* count;
+    int32_t* status;
+};
+
+template <int L>
+struct ConvShape {
+    static constexpr int T = L / 16;
+    static constexpr int Q = L / 256;
+    static constexpr int X1S = 16 * (T + Q);
+    static constexpr int G = 16 * (Q + 1) + Q;
+    static constexpr int X2S = 16 * G;
+    static constexpr int BUFS = X1S > X2S ? X1S : X2S;
+    static constexpr int TW3 = 16 * (Q + 1);
+    static constexpr size_t smem_bytes = (size_t)(2 * BUFS + L + TW3) * sizeof(float2);
+};
+
+__device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, float v) {
+    int idx = atomicAdd(A.count, 1);
+    if (idx < A.cap) {
+        fdas_cand c;
+        c.z_idx = row;
+        c.col = (int32_t)col;
+        c.power = v;
+        c.flags = 0;
+        A.cand[idx] = c;
+    } else if (A.status) {
+        atomicOr(A.status, FDAS_STATUS_OVERFLOW);
+    }
+}
+
+template <int L, bool FUSE>
+__global__ void __launch_bounds__(L / 16) conv_kernel(const ConvArgs A) {
+    using S = ConvShape<L>;
+    constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = 16 / Q;
+    extern __shared__ float4 smem4[];
+    float2* buf0 = reinterpret_cast<float2*>(smem4);
+    float2* buf1 = buf0 + BUFS;
+    float2* outb = buf1 + BUFS;
+    float2* tw3 = outb + L;
+
+    const int t = threadIdx.x;
+    const int a = t / Q, c = t % Q;
+    const int M = A.M, B = L - M;
+
+    // inverse pass-3' twiddles: tw3[k1*(Q+1) + n2] = exp(+i 2 pi n2 k1 / (L/16))
+    for (int idx = t; idx < S::TW3; idx += T) {
+        int k1 = idx / (Q + 1), n2 = idx % (Q + 1);
+        float sn, cs;
+        sincospif(2.0f * (float)((n2 * k1) % (L / 16)) / (float)(L / 16), &sn, &cs);
+        tw3[idx] = make_float2(cs, sn);
+    }
+    // inverse pass-2' twiddles (thread (a, c), reg n1): exp(+i 2 pi (n1 Q + c) a / L)
+    float2 tw2[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        float sn, cs;
+        sincospif(2.0f * (float)(((n1 * Q + c) * a) % L) / (float)L, &sn, &cs);
+        tw2[n1] = make_float2(cs, sn);
+    }
+    // partner thread holding -k for the conjugate (z < 0) templates
+    const int tp = (a != 0) ? (16 - a) * Q + (Q - 1 - c) : (Q - c) % Q;
+    __syncthreads();
+
+    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
+    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
+    int64_t cur_seg = -1;
+    int parity = 0;
+    float2 Y[16];
+    float2 v[16];
+
+    for (int64_t w = lo; w < hi; ++w) {
+        const int64_t s = w / A.K;
+        const int q = (int)(w - s * A.K);
+        if (s != cur_seg) {
+            // ---- forward FFT of segment s (once per segment) ----
+            cur_seg = s;
+            const int64_t base = s * (int64_t)B - M / 2;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                int64_t pos = base + i * T + t;
+                v[i] = (pos >= 0 && pos < A.nb) ? __ldg(&A.spec[pos]) : make_float2(0.f, 0.f);
+            }
+            dft16<-1>(v);
+#pragma unroll
+            for (int k0 = 1; k0 < 16; ++k0) {
+                float sn, cs;
+                sincospif(2.0f * (float)(t * k0) / (float)L, &sn, &cs);
+                v[k0] = cmul(v[k0], make_float2(cs, -sn));
+            }
+            __syncthreads();   // previous users of buf0 / buf1 are done
+#pragma unroll
+            for (int i = 0; i < 16; ++i) buf0[i * (T + Q) + t] = v[i];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = buf0[a * (T + Q) + i * Q + c];
+            dft16<-1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < 16; ++k1) {
+                float sn, cs;
+                sincospif(2.0f * (float)((c * k1) % (L / 16)) / (float)(L / 16), &sn, &cs);
+                v[k1] = cmul(v[k1], make_float2(cs, -sn));
+            }
+            float2* x2 = buf1 + a * G;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x2[i * (Q + 1) + c] = v[i];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = x2[(c + Q * (i / Q)) * (Q + 1) + (i % Q)];
+#pragma unroll
+            for (int s2 = 0; s2 < NS; ++s2) dftq<Q, -1>(v + s2 * Q);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) Y[i] = v[i];
+            __syncthreads();   // buffers free for the template loop
+            parity = 0;
+        }
+
+        // ---- template row for item q ----
+        int row, brow, cj;
+        if (!A.sym) {
+            row = q; brow = q; cj = 0;
+        } else if (A.zero) {
+            if (q == 0) { brow = 0; cj = 0; }
+            else { brow = (q + 1) >> 1; cj = (q & 1) ? 0 : 1; }
+            row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
+        } else {
+            brow = q >> 1; cj = q & 1;
+            row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
+        }
+
+        // ---- multiply by the template spectrum (bank row via L2) ----
+        const float4* hb = A.bank + (size_t)brow * (L / 2);
+        if (!cj) {
+#pragma unroll
+            for (int ip = 0; ip < 8; ++ip) {
+                float4 h = __ldg(&hb[ip * T + t]);
+                v[2 * ip] = cmul(Y[2 * ip], make_float2(h.x, h.y));
+                v[2 * ip + 1] = cmul(Y[2 * ip + 1], make_float2(h.z, h.w));
+            }
+        } else if (t != 0) {
+#pragma unroll
+            for (int ip = 0; ip < 8; ++ip) {
+                float4 h = __ldg(&hb[(7 - ip) * T + tp]);
+                v[2 * ip] = cmulc(Y[2 * ip], make_float2(h.z, h.w));
+                v[2 * ip + 1] = cmulc(Y[2 * ip + 1], make_float2(h.x, h.y));
+            }
+        } else {
+            const float2* hb2 = reinterpret_cast<const float2*>(hb);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int ii = (i < Q) ? ((Q - i) % Q) : (15 + Q - i);
+                v[i] = cmulc(Y[i], __ldg(&hb2[2 * ((ii >> 1) * T) + (ii & 1)]));
+            }
+        }
+
+        // ---- inverse pass 3': radix Q over k2, then twiddle ----
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) {
+            dftq<Q, 1>(v + s2 * Q);
+#pragma unroll
+            for (int n2 = 1; n2 < Q; ++n2)
+                v[s2 * Q + n2] = cmul(v[s2 * Q + n2], tw3[(c + Q * s2) * (Q + 1) + n2]);
+        }
+        // ---- D3 -> D2 inside the Q-thread group ----
+        {
+            float2* x2 = (parity ? buf0 : buf1) + a * G;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x2[(c + Q * (i / Q)) * (Q + 1) + (i % Q)] = v[i];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = x2[i * (Q + 1) + c];
+        }
+        // ---- inverse pass 2': radix 16 over k1, then twiddle ----
+        dft16<1>(v);
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = cmul(v[n1], tw2[n1]);
+        // ---- D2 -> D1 across the CTA ----
+        {
+            float2* x1 = parity ? buf1 : buf0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x1[a * (T + Q) + i * Q + c] = v[i];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = x1[i * (T + Q) + t];
+        }
+        // ---- inverse pass 1': radix 16 over k0 -> natural order ----
+        dft16<1>(v);
+#pragma unroll
+        for (int n0 = 0; n0 < 16; ++n0) outb[n0 * T + t] = v[n0];
+        __syncthreads();
+
+        // ---- epilogue: powers of positions M/2 .. M/2+B (pairs of bins) ----
+        const int64_t r0 = s * (int64_t)B;
+        float* prow = A.plane + (int64_t)row * A.row_stride;
+        const int NP = B / 2;
+        const float hs = 0.61685027506808491f;   // (pi/4)^2
+        for (int p = t; p < NP; p += T) {
+            const int j = M / 2 + 2 * p;
+            const float4 x01 = *reinterpret_cast<const float4*>(&outb[j]);
+            const float2 xn = outb[j + 2];
+            const float dx0 = x01.x - x01.z, dy0 = x01.y - x01.w;
+            const float dx1 = x01.z - xn.x, dy1 = x01.w - xn.y;
+            float p0 = fmaf(x01.x, x01.x, x01.y * x01.y);
+            float p1 = fmaf(x01.z, x01.z, x01.w * x01.w);
+            float h0 = hs * fmaf(dx0, dx0, dy0 * dy0);
+            float h1 = hs * fmaf(dx1, dx1, dy1 * dy1);
+            const int64_t r = r0 + 2 * p;
+            if (r + 2 < A.nb) {
+                if (A.interbin) {
+                    *reinterpret_cast<float4*>(prow + 2 * r) = make_float4(p0, h0, p1, h1);
+                } else {
+                    *reinterpret_cast<float2*>(prow + r) = make_float2(p0, p1);
+                }
+            } else if (r < A.nb) {
+                // the last bins of the row: no r+1 beyond nb-1
+                if (r + 1 >= A.nb - 1) h1 = 0.f;
+                if (r >= A.nb - 1) h0 = 0.f;
+                if (A.interbin) {
+                    prow[2 * r] = p0;
+                    prow[2 * r + 1] = h0;
+                    if (r + 1 < A.nb) { prow[2 * r + 2] = p1; prow[2 * r + 3] = h1; }
+                } else {
+                    prow[r] = p0;
+                    if (r + 1 < A.nb) prow[r + 1] = p1;
+                }
+                if (r + 1 >= A.nb) { p1 = 0.f; h1 = 0.f; }
+            } else {
+                p0 = p1 = h0 = h1 = 0.f;
+            }
+            if constexpr (FUSE) {
+                float m = fmaxf(fmaxf(p0, p1), fmaxf(h0, h1));
+                if (m > A.thr) {
+                    if (A.interbin) {
+                        if (p0 > A.thr) emit(A, row, 2 * r, p0);
+                        if (h0 > A.thr) emit(A, row, 2 * r + 1, h0);
+                        if (p1 > A.thr) emit(A, row, 2 * r + 2, p1);
+                        if (h1 > A.thr) emit(A, row, 2 * r + 3, h1);
+                    } else {
+                        if (p0 > A.thr) emit(A, row, r, p0);
+                        if (p1 > A.thr) emit(A, row, r + 1, p1);
+                    }
+                }
+            }
+        }
+        parity ^= 1;
+    }
+}
+
+template <int L, bool FUSE>
+static int launch_one(const ConvArgs& args, cudaStream_t st) {
+    using S = ConvShape<L>;
+    static int grid = 0;
+    if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::smem_bytes);
+        if (e != cudaSuccess) return FDAS_E_CUDA;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return FDAS_E_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE>, S::T,
+                                                          S::smem_bytes) != cudaSuccess)
+            return FDAS_E_CUDA;
+        if (per_sm < 1) return FDAS_E_UNSUPPORTED;
+        grid = sms * per_sm;
+    }
+    int64_t g = std::min<int64_t>(grid, std::max<int64_t>(1, args.items));
+    conv_kernel<L, FUSE><<<(unsigned)g, S::T, S::smem_bytes, st>>>(args);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
+                     const float4* bank, float* plane, int64_t row_stride,
+                     const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st) {
+    ConvArgs a;
+    a.spec = spec;
+    a.nb = nb;
+    a.bank = bank;
+    a.plane = plane;
+    a.row_stride = row_stride;
+    const int64_t B = p->L - p->M;
+    const int64_t nseg = (nb + B - 1) / B;
+    a.items = nseg * g.K;
+    a.K = g.K;
+    a.j0 = g.j0;
+    a.sym = g.sym;
+    a.zero = g.zero;
+    a.M = p->M;
+    a.interbin = p->interbin;
+    a.thr = fused ? fused->thr : 0.f;
+    a.cand = fused ? fused->out : nullptr;
+    a.cap = fused ? fused->cap : 0;
+    a.count = fused ? fused->count : nullptr;
+    a.status = status;
+    if (fused) {
+        cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return FDAS_E_CUDA;
+    }
+    const bool f = fused != nullptr;
+    switch (p->L) {
+        case 1024: return f ? launch_one<1024, true>(a, st) : launch_one<1024, false>(a, st);
+        case 2048: return f ? launch_one<2048, true>(a, st) : launch_one<2048, false>(a, st);
+        case 4096: return f ? launch_one<4096, true>(a, st) : launch_one<4096, false>(a, st);
+        default: return FDAS_E_INVAL;
+    }
+}
+
+}  // namespace fdas

@@ -1,0 +1,141 @@
+// Register-resident small DFTs (radix 2/4/8/16) used by the convolver and
+// the front end.  S = -1 is the forward transform  X_k = sum_n x_n e^{-i2pi nk/N},
+// S = +1 the inverse without 1/N  (DFT and IDFT of Section 4.2).  Inputs and
+// outputs are in natural order; all indices are compile-time constants so
+// the permutations are register renames.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fdas {
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// a * b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// (S i) * v
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 v) {
+    return S > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+
+constexpr float kC8 = 0.92387953251128674f;  // cos(pi/8)
+constexpr float kS8 = 0.38268343236508978f;  // sin(pi/8)
+constexpr float kR2 = 0.70710678118654752f;  // 1/sqrt(2)
+
+// v * w16^m,  w16 = exp(S i 2 pi / 16),  m a compile-time constant
+template <int S, int MM>
+__device__ __forceinline__ float2 w16(float2 v) {
+    constexpr int m = ((MM % 16) + 16) % 16;
+    constexpr float sg = (float)S;
+    if constexpr (m == 0) {
+        return v;
+    } else if constexpr (m == 4) {
+        return mul_si<S>(v);
+    } else if constexpr (m == 8) {
+        return make_float2(-v.x, -v.y);
+    } else if constexpr (m == 12) {
+        return mul_si<-S>(v);
+    } else if constexpr (m == 2) {            // (1 + S i)/sqrt2
+        return make_float2((v.x - sg * v.y) * kR2, (v.y + sg * v.x) * kR2);
+    } else if constexpr (m == 6) {            // (-1 + S i)/sqrt2
+        return make_float2((-v.x - sg * v.y) * kR2, (-v.y + sg * v.x) * kR2);
+    } else if constexpr (m == 10) {           // (-1 - S i)/sqrt2
+        return make_float2((-v.x + sg * v.y) * kR2, (-v.y - sg * v.x) * kR2);
+    } else if constexpr (m == 14) {           // (1 - S i)/sqrt2
+        return make_float2((v.x + sg * v.y) * kR2, (v.y - sg * v.x) * kR2);
+    } else {
+        // odd m: cos/sin of 2 pi m/16 from the two octant constants
+        constexpr float c = (m == 1 || m == 15) ? kC8 : (m == 3 || m == 13) ? kS8
+                          : (m == 5 || m == 11) ? -kS8 : -kC8;
+        constexpr float s0 = (m == 1 || m == 7) ? kS8 : (m == 3 || m == 5) ? kC8
+                           : (m == 9 || m == 15) ? -kS8 : -kC8;
+        constexpr float s = sg * s0;
+        return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = a - b;
+    a = a + b;
+    b = t;
+}
+
+template <int S>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    float2 s02 = x0 + x2, d02 = x0 - x2, s13 = x1 + x3;
+    float2 d13 = mul_si<S>(x1 - x3);
+    x0 = s02 + s13;
+    x2 = s02 - s13;
+    x1 = d02 + d13;
+    x3 = d02 - d13;
+}
+
+// 8 points: n = 2 n1 + n2, k = k1 + 4 k2
+template <int S>
+__device__ __forceinline__ void dft8(float2* v) {
+    dft4<S>(v[0], v[2], v[4], v[6]);
+    dft4<S>(v[1], v[3], v[5], v[7]);
+    v[3] = w16<S, 2>(v[3]);
+    v[5] = w16<S, 4>(v[5]);
+    v[7] = w16<S, 6>(v[7]);
+    dft2<S>(v[0], v[1]);
+    dft2<S>(v[2], v[3]);
+    dft2<S>(v[4], v[5]);
+    dft2<S>(v[6], v[7]);
+    // X[k1 + 4 k2] sits in v[2 k1 + k2]
+    float2 t1 = v[1], t2 = v[2], t3 = v[3], t4 = v[4], t5 = v[5], t6 = v[6];
+    v[1] = t2;
+    v[2] = t4;
+    v[3] = t6;
+    v[4] = t1;
+    v[5] = t3;
+    v[6] = t5;
+}
+
+// 16 points: n = 4 n1 + n2, k = k1 + 4 k2
+template <int S>
+__device__ __forceinline__ void dft16(float2* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<S>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    v[5] = w16<S, 1>(v[5]);
+    v[6] = w16<S, 2>(v[6]);
+    v[7] = w16<S, 3>(v[7]);
+    v[9] = w16<S, 2>(v[9]);
+    v[10] = w16<S, 4>(v[10]);
+    v[11] = w16<S, 6>(v[11]);
+    v[13] = w16<S, 3>(v[13]);
+    v[14] = w16<S, 6>(v[14]);
+    v[15] = w16<S, 9>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // X[k1 + 4 k2] sits in v[4 k1 + k2]: transpose the 4x4
+    float2 t;
+    t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[2]; v[2] = v[8]; v[8] = t;
+    t = v[3]; v[3] = v[12]; v[12] = t;
+    t = v[6]; v[6] = v[9]; v[9] = t;
+    t = v[7]; v[7] = v[13]; v[13] = t;
+    t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <int Q, int S>
+__device__ __forceinline__ void dftq(float2* v) {
+    if constexpr (Q == 4) {
+        dft4<S>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (Q == 8) {
+        dft8<S>(v);
+    } else {
+        static_assert(Q == 16, "radix");
+        dft16<S>(v);
+    }
+}
+
+}  // namespace fdas

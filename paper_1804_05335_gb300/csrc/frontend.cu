@@ -1,0 +1,283 @@
+// fdas_normalise: real FFT of the series and block running-median
+// normalisation (Section 3 workflow; Section 4.1 real-to-complex transform;
+// DFT sign of Section 4.2).
+//
+// The n real samples are read as N = n/2 complex values z_m = x_2m + i x_2m+1
+// and transformed by a three-pass N-point FFT, N = N1 N2 N3 (each factor
+// 16..256):
+//   index n = n1 + N1 n2 + N1 N2 n3, frequency k = k3 + N3 k2 + N3 N2 k1;
+//   pass A: length-N3 DFTs over n3, twiddle exp(-i 2 pi (n1 + N1 n2) k3 / N);
+//   pass B: length-N2 DFTs over n2, twiddle exp(-i 2 pi n1 k2 / (N1 N2));
+//   pass C: length-N1 DFTs over n1, written transposed to natural order.
+// Each pass moves tiles of 16 lines x R points through shared memory with
+// 128-byte coalesced rows and runs a radix-2 Stockham (self-sorting) DFT on
+// the tile.  A final kernel per median block forms the real spectrum
+//   X_k = E_k + exp(-i 2 pi k / n) O_k,  E = (Z_k + conj Z_{N-k})/2,
+//   O = (Z_k - conj Z_{N-k}) / 2i,   X_0 := 0,
+// selects the lower median of |X_k|^2 in the block exactly (radix select on
+// the float bit patterns) and scales the block by sqrt(ln 2 / median).
+#include <math.h>
+
+#include "internal.h"
+
+namespace fdas {
+
+constexpr int kFeThreads = 256;
+constexpr int kTilePad = 17;   // tile row stride in float2 (16 lines + 1)
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Forward length-R DFT of the 16 columns of tile x[r*17 + col]; returns the
+// buffer that holds the result (x or y).  tw[q] = exp(-i 2 pi q / R), q < R/2.
+__device__ float2* tile_dft(float2* x, float2* y, const float2* tw, int R) {
+    const int nb = 8 * R;   // butterflies per stage over 16 columns
+    for (int l = R / 2, m = 1; l >= 1; l >>= 1, m <<= 1) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int col = b & 15, bf = b >> 4;
+            const int j = bf / m, k = bf - j * m;
+            const float2 w = tw[j * m];
+            const float2 c0 = x[(k + j * m) * kTilePad + col];
+            const float2 c1 = x[(k + j * m + l * m) * kTilePad + col];
+            y[(k + 2 * j * m) * kTilePad + col] = c_add(c0, c1);
+            y[(k + 2 * j * m + m) * kTilePad + col] = c_mul(w, c_sub(c0, c1));
+        }
+        __syncthreads();
+        float2* t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+__device__ void load_tw(float2* tw, int R) {
+    for (int q = threadIdx.x; q < R / 2; q += blockDim.x) {
+        float s, c;
+        sincospif(2.0f * (float)q / (float)R, &s, &c);
+        tw[q] = make_float2(c, -s);
+    }
+}
+
+// exp(-i 2 pi e / N) with 0 <= e < N (N a power of two, e exact in float)
+__device__ __forceinline__ float2 twiddle(int64_t e, int64_t N) {
+    float s, c;
+    sincospif(2.0f * (float)e / (float)N, &s, &c);
+    return make_float2(c, -s);
+}
+
+// pass A: DFT over n3 (length N3, stride N12), 16 consecutive lines m per CTA
+__global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict__ in,
+                                                        float2* __restrict__ out, int N3,
+                                                        int64_t N12, int64_t N) {
+    extern __shared__ float2 fsm[];
+    float2* tw = fsm;
+    float2* x = tw + 128;
+    float2* y = x + 256 * kTilePad;
+    const int64_t m0 = (int64_t)blockIdx.x * 16;
+    load_tw(tw, N3);
+    for (int idx = threadIdx.x; idx < 16 * N3; idx += blockDim.x) {
+        const int col = idx & 15, r = idx >> 4;
+        x[r * kTilePad + col] = in[m0 + col + r * N12];
+    }
+    __syncthreads();
+    float2* res = tile_dft(x, y, tw, N3);
+    for (int idx = threadIdx.x; idx < 16 * N3; idx += blockDim.x) {
+        const int col = idx & 15, k3 = idx >> 4;
+        const int64_t m = m0 + col;
+        out[m + k3 * N12] = c_mul(res[k3 * kTilePad + col], twiddle((m * k3) % N, N));
+    }
+}
+
+// pass B: DFT over n2 (length N2, stride N1), in place; 16 consecutive n1 per CTA
+__global__ void __launch_bounds__(kFeThreads) fe_pass_b(float2* __restrict__ buf, int N1, int N2) {
+    extern __shared__ float2 fsm[];
+    float2* tw = fsm;
+    float2* x = tw + 128;
+    float2* y = x + 256 * kTilePad;
+    const int chunks = N1 / 16;
+    const int64_t k3 = blockIdx.x / chunks;
+    const int n10 = (blockIdx.x % chunks) * 16;
+    const int64_t N12 = (int64_t)N1 * N2;
+    const int64_t base = k3 * N12 + n10;
+    load_tw(tw, N2);
+    for (int idx = threadIdx.x; idx < 16 * N2; idx += blockDim.x) {
+        const int col = idx & 15, r = idx >> 4;
+        x[r * kTilePad + col] = buf[base + col + (int64_t)r * N1];
+    }
+    __syncthreads();
+    float2* res = tile_dft(x, y, tw, N2);
+    for (int idx = threadIdx.x; idx < 16 * N2; idx += blockDim.x) {
+        const int col = idx & 15, k2 = idx >> 4;
+        const int64_t e = ((int64_t)(n10 + col) * k2) % N12;
+        buf[base + col + (int64_t)k2 * N1] = c_mul(res[k2 * kTilePad + col], twiddle(e, N12));
+    }
+}
+
+// pass C: DFT over n1 (contiguous, length N1); 16 consecutive k3 per CTA,
+// written to natural order X[k3 + N3 k2 + N3 N2 k1]
+__global__ void __launch_bounds__(kFeThreads) fe_pass_c(const float2* __restrict__ in,
+                                                        float2* __restrict__ out, int N1, int N2,
+                                                        int N3) {
+    extern __shared__ float2 fsm[];
+    float2* tw = fsm;
+    float2* x = tw + 128;
+    float2* y = x + 256 * kTilePad;
+    const int chunks = N3 / 16;
+    const int64_t k2 = blockIdx.x / chunks;
+    const int64_t k30 = (int64_t)(blockIdx.x % chunks) * 16;
+    const int64_t N12 = (int64_t)N1 * N2;
+    load_tw(tw, N1);
+    for (int idx = threadIdx.x; idx < 16 * N1; idx += blockDim.x) {
+        const int r = idx % N1, col = idx / N1;
+        x[r * kTilePad + col] = in[(k30 + col) * N12 + k2 * N1 + r];
+    }
+    __syncthreads();
+    float2* res = tile_dft(x, y, tw, N1);
+    const int64_t N32 = (int64_t)N3 * N2;
+    for (int idx = threadIdx.x; idx < 16 * N1; idx += blockDim.x) {
+        const int col = idx & 15, k1 = idx >> 4;
+        out[k30 + col + N3 * k2 + N32 * k1] = res[k1 * kTilePad + col];
+    }
+}
+
+// Exact rank-`rank` element of keys[0..len) (unsigned order) by 8-bit radix
+// select; every thread of the CTA returns it.
+__device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32_t* hist,
+                                 int* bc) {
+    uint32_t prefix = 0, pmask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t k = keys[i];
+            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            uint32_t h[8], sum = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) { h[e] = hist[8 * l + e]; sum += h[e]; }
+            uint32_t inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (l >= o) inc += v;
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, inc > (uint32_t)rank);
+            const int L0 = __ffs(hit) - 1;
+            if (l == L0) {
+                uint32_t base = inc - sum;
+                int d = 0;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if (base + h[e] > (uint32_t)rank) { d = e; break; }
+                    base += h[e];
+                }
+                bc[0] = 8 * l + d;
+                bc[1] = rank - (int)base;
+            }
+        }
+        __syncthreads();
+        const uint32_t dig = (uint32_t)bc[0];
+        rank = bc[1];
+        prefix |= dig << shift;
+        pmask |= 255u << shift;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// one CTA per median block: real-spectrum post-processing + normalisation
+__global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__ Z,
+                                                      float2* __restrict__ spec, int64_t N,
+                                                      int block) {
+    extern __shared__ float2 psm[];
+    float2* xs = psm;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(xs + block);
+    __shared__ uint32_t hist[256];
+    __shared__ int bc[2];
+    const int64_t k0 = (int64_t)blockIdx.x * block;
+    const int len = (int)min((int64_t)block, N - k0);
+    const int64_t n = 2 * N;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int64_t k = k0 + i;
+        const float2 zk = Z[k];
+        const float2 zm = Z[(N - k) & (N - 1)];
+        const float ex = 0.5f * (zk.x + zm.x), ey = 0.5f * (zk.y - zm.y);
+        const float ox = 0.5f * (zk.y + zm.y), oy = -0.5f * (zk.x - zm.x);
+        float s, c;
+        sincospif(2.0f * (float)k / (float)n, &s, &c);
+        // w = (c, -s):  X = E + w O
+        float2 X = make_float2(ex + fmaf(c, ox, s * oy), ey + fmaf(c, oy, -s * ox));
+        if (k == 0) X = make_float2(0.f, 0.f);
+        xs[i] = X;
+        keys[i] = __float_as_uint(fmaf(X.x, X.x, X.y * X.y));
+    }
+    __syncthreads();
+    const uint32_t mk = radix_select(keys, len, (len - 1) / 2, hist, bc);
+    const float med = __uint_as_float(mk);
+    const float scale = med > 0.f ? sqrtf(0.69314718055994531f / med) : 0.f;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const float2 X = xs[i];
+        spec[k0 + i] = make_float2(X.x * scale, X.y * scale);
+    }
+}
+
+static int log2i(int64_t v) {
+    int p = 0;
+    while (((int64_t)1 << p) < v) ++p;
+    return p;
+}
+
+}  // namespace fdas
+
+using namespace fdas;
+
+extern "C" {
+
+size_t fdas_normalise_workspace_bytes(int64_t n) {
+    if (n < (1 << 13) || n > ((int64_t)1 << 25) || (n & (n - 1))) return 0;
+    return (size_t)(n / 2) * sizeof(float2);
+}
+
+int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* spec, void* work,
+                   size_t work_bytes, void* stream) {
+    if (!series || !spec || !work) return FDAS_E_INVAL;
+    const size_t need = fdas_normalise_workspace_bytes(n);
+    if (need == 0 || work_bytes < need) return FDAS_E_INVAL;
+    if (median_block < 32 || median_block > 8192) return FDAS_E_INVAL;
+    if (!aligned(series, 8) || !aligned(spec, 8) || !aligned(work, 16)) return FDAS_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = n / 2;
+    const int p = log2i(N);
+    const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
+    const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
+    const int64_t N12 = (int64_t)N1 * N2;
+    const size_t tile_sm = (128 + 2 * 256 * kTilePad) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(fe_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
+            cudaFuncSetAttribute(fe_pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
+            cudaFuncSetAttribute(fe_pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
+            cudaFuncSetAttribute(fe_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 8192 * (int)(sizeof(float2) + sizeof(uint32_t))))
+            return FDAS_E_CUDA;
+        attr = true;
+    }
+    float2* sp = reinterpret_cast<float2*>(spec);
+    float2* wk = reinterpret_cast<float2*>(work);
+    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_sm, st>>>(
+        reinterpret_cast<const float2*>(series), sp, N3, N12, N);
+    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_sm, st>>>(sp, N1, N2);
+    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_sm, st>>>(sp, wk, N1, N2, N3);
+    const int nblk = (int)((N + median_block - 1) / median_block);
+    const size_t post_sm = (size_t)median_block * (sizeof(float2) + sizeof(uint32_t));
+    fe_post<<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

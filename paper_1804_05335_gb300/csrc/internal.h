@@ -1,0 +1,33 @@
+// Library-internal declarations shared by the FDAS translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdas.h"
+
+namespace fdas {
+
+// Template grid and bank-row bookkeeping derived from fdas_params.
+struct Grid {
+    int32_t K;       // templates (plane rows)
+    int32_t Kb;      // bank rows
+    int32_t j0;      // number of z < 0 rows served by conjugation (symmetric grid), else 0
+    int32_t sym;     // 1: symmetric grid, bank holds z >= 0 only
+    int32_t zero;    // 1: z = 0 is on a symmetric grid
+    int32_t hmax;    // largest half-width on the grid
+};
+
+// Validates p; returns FDAS_OK and fills g, or FDAS_E_INVAL.
+int make_grid(const fdas_params* p, Grid* g);
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_E_CUDA; }
+
+inline bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// Launchers implemented in the .cu files.
+int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st);
+int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
+                     const float4* bank, float* plane, int64_t row_stride,
+                     const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st);
+
+}  // namespace fdas

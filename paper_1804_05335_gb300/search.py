@@ -1,0 +1,87 @@
+"""Device buffers for one FDAS search and the calls that fill them.
+
+A convenience layer over the C ABI: torch provides the device memory and the
+stream, the library's kernels do all the work.  One ``Search`` holds, for a
+series of n samples: the series, the normalised spectrum (n/2 bins), the
+front-end workspace, the template bank, the f-fdot plane (K rows) and a
+candidate buffer.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (fdas_bank_rows, fdas_correlate, fdas_fused_threshold, fdas_make_templates,
+               fdas_normalise, fdas_normalise_workspace_bytes, fdas_num_segments,
+               fdas_num_templates, fdas_plane_width, fdas_threshold, params)
+
+
+class Search:
+    def __init__(self, n: int, L: int, M: int, zmin: int, zmax: int, zstep: int,
+                 interbin: int = 1, median_block: int = 1024, thr: float = 20.0,
+                 cap: int = 1 << 16, device="cuda", plane: bool = True):
+        self.n = int(n)
+        self.nb = self.n // 2
+        self.p = params(L, M, zmin, zmax, zstep, interbin)
+        self.K = fdas_num_templates(self.p)
+        self.Kb = fdas_bank_rows(self.p)
+        self.L, self.M = int(L), int(M)
+        self.median_block = int(median_block)
+        self.thr = float(thr)
+        self.cap = int(cap)
+        self.width = fdas_plane_width(self.p, self.nb)
+        self.row_stride = (self.width + 3) // 4 * 4
+        self.nseg = fdas_num_segments(self.p, self.nb)
+        dev = torch.device(device)
+        self.device = dev
+        self.series = torch.empty(self.n, dtype=torch.float32, device=dev)
+        self.spec = torch.empty(self.nb, dtype=torch.complex64, device=dev)
+        self.work_bytes = fdas_normalise_workspace_bytes(self.n)
+        self.work = torch.empty(max(self.work_bytes, 16), dtype=torch.uint8, device=dev)
+        self.bank = torch.empty(self.Kb * self.L * 2, dtype=torch.float32, device=dev)
+        self.plane = (torch.empty(self.K * self.row_stride, dtype=torch.float32, device=dev)
+                      if plane else None)
+        self.cand = torch.empty(self.cap * 4, dtype=torch.int32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.fused = fdas_fused_threshold(self.thr, int(self.cand.data_ptr()), self.cap,
+                                          int(self.count.data_ptr()))
+
+    # ---- the calls ----
+    def make_templates(self, stream=None):
+        fdas_make_templates(self.p, self.bank, stream)
+
+    def normalise(self, stream=None):
+        fdas_normalise(self.series, self.n, self.median_block, self.spec, self.work,
+                       self.work_bytes, stream)
+
+    def correlate(self, fused: bool = True, spec=None, nb=None, stream=None):
+        fdas_correlate(self.p, self.spec if spec is None else spec,
+                       self.nb if nb is None else nb, self.bank, self.plane, self.row_stride,
+                       self.fused if fused else None, self.status, stream)
+
+    def threshold(self, want_peaks: bool = True, stream=None):
+        fdas_threshold(self.plane, self.K, self.width, self.row_stride, self.thr,
+                       1 if want_peaks else 0, self.cand, self.cap, self.count, self.status,
+                       stream)
+
+    def step(self, stream=None):
+        """One pass of the hot path: bank, spectrum, plane + fused candidates."""
+        self.make_templates(stream)
+        self.normalise(stream)
+        self.correlate(True, stream=stream)
+
+    # ---- views ----
+    def plane2d(self) -> torch.Tensor:
+        return self.plane.view(self.K, self.row_stride)[:, : self.width]
+
+    def candidates(self):
+        """(rows, cols, power, flags, total) sorted by (row, col); syncs."""
+        total = int(self.count.item())
+        k = min(total, self.cap)
+        c = self.cand[: 4 * k].view(k, 4).cpu().numpy()
+        rows, cols = c[:, 0].copy(), c[:, 1].copy()
+        pw = c[:, 2].copy().view(np.float32)
+        fl = c[:, 3].copy()
+        o = np.lexsort((cols, rows))
+        return rows[o], cols[o], pw[o], fl[o], total

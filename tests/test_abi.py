@@ -1,0 +1,99 @@
+"""CPU checks of the C-ABI library: it loads, exports what include/fdas.h
+declares, and its host-side bookkeeping and argument validation behave.
+
+No call here launches GPU work: every compute entry point is called only with
+arguments that its validation rejects before anything reaches CUDA.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1804_05335_gb300 as F
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1804_05335_gb300 import build
+    build.build()
+    F.load_library()
+
+
+def test_library_exports_every_declared_function():
+    lib = ctypes.CDLL(F.lib_path())
+    names = F.header_functions()
+    assert "fdas_correlate" in names and "fdas_make_templates" in names
+    for n in ("fdas_normalise", "fdas_threshold"):
+        assert n in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_helpers():
+    p = F.params(2048, 256, -200, 200, 2, 1)
+    assert F.fdas_num_templates(p) == 201
+    assert F.fdas_bank_rows(p) == 101
+    assert F.fdas_num_segments(p, 1 << 22) == -(-(1 << 22) // 1792)
+    assert F.fdas_plane_width(p, 1 << 22) == 1 << 23
+    assert F.fdas_plane_width(F.params(2048, 256, -200, 200, 2, 0), 1000) == 1000
+    assert F.fdas_bank_rows(F.params(2048, 64, -21, 21, 2, 1)) == 11       # no z = 0
+    assert F.fdas_bank_rows(F.params(2048, 64, -10, 20, 2, 1)) == 16       # asymmetric: all rows
+    assert [F.fdas_half_width(z) for z in (0, 1, -21, 200)] == [8, 9, 19, 108]
+    assert F.fdas_normalise_workspace_bytes(1 << 23) == (1 << 22) * 8
+    assert F.fdas_normalise_workspace_bytes(1000) == 0
+    assert F.fdas_strerror(F.FDAS_E_INVAL) == "invalid argument"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(L=512), dict(L=3000), dict(M=60), dict(M=66), dict(M=4096),
+    dict(zstep=0), dict(zmin=10, zmax=-10), dict(zmin=-5, zmax=6, zstep=2),
+    dict(interbin=2), dict(zmin=-300, zmax=300, M=256),          # h(300) = 158 > 127
+])
+def test_invalid_params_rejected(bad):
+    kw = dict(L=2048, M=256, zmin=-200, zmax=200, zstep=2, interbin=1)
+    kw.update(bad)
+    p = F.params(**kw)
+    with pytest.raises(F.FdasError) as e:
+        F.fdas_num_templates(p)
+    assert e.value.code == F.FDAS_E_INVAL
+    with pytest.raises(F.FdasError) as e:
+        F.fdas_correlate(p, 256, 1000, 256, 256, 2000, stream=0)
+    assert e.value.code == F.FDAS_E_INVAL
+
+
+def test_invalid_buffers_rejected_before_launch():
+    p = F.params(2048, 256, -200, 200, 2, 1)
+    cases = [
+        lambda: F.fdas_correlate(p, 0, 1000, 256, 256, 2000, stream=0),       # NULL spec
+        lambda: F.fdas_correlate(p, 256, 1000, 264, 256, 2000, stream=0),     # bank not 16-aligned
+        lambda: F.fdas_correlate(p, 256, 1000, 256, 256, 1998, stream=0),     # stride < width
+        lambda: F.fdas_correlate(p, 256, 1000, 256, 256, 2002, stream=0),     # stride % 4
+        lambda: F.fdas_correlate(p, 256, 0, 256, 256, 2000, stream=0),        # nb < 1
+        lambda: F.fdas_make_templates(p, 0, stream=0),
+        lambda: F.fdas_make_templates(p, 8, stream=0),
+        lambda: F.fdas_normalise(256, 1000, 1024, 256, 256, 1 << 20, stream=0),    # n not 2^k
+        lambda: F.fdas_normalise(256, 1 << 14, 16, 256, 256, 1 << 20, stream=0),   # block
+        lambda: F.fdas_normalise(256, 1 << 14, 1024, 256, 256, 100, stream=0),     # work size
+        lambda: F.fdas_threshold(256, 0, 10, 10, 20.0, 0, 256, 4, 256, stream=0),  # rows
+        lambda: F.fdas_threshold(256, 3, 10, 9, 20.0, 0, 256, 4, 256, stream=0),   # stride
+        lambda: F.fdas_threshold(256, 3, 10, 10, 20.0, 4, 256, 4, 256, stream=0),  # flags
+    ]
+    for f in cases:
+        with pytest.raises(F.FdasError) as e:
+            f()
+        assert e.value.code == F.FDAS_E_INVAL
+
+
+def _slot(k, L):
+    """Bank storage slot of frequency k, restated from the layout in fdas.h."""
+    Q, T = L // 256, L // 16
+    a, k1, c2 = k % 16, (k // 16) % 16, k // 256
+    c1, s2 = k1 % Q, k1 // Q
+    t, i = a * Q + c1, s2 * Q + c2
+    return 2 * ((i // 2) * T + t) + (i % 2)
+
+
+@pytest.mark.parametrize("L", [1024, 2048, 4096])
+def test_bank_layout_is_a_permutation(L):
+    s = np.array([_slot(k, L) for k in range(L)])
+    assert sorted(s) == list(range(L))
