@@ -258,14 +258,15 @@ def run_native(args):
     # keep the GPU busy a moment so the clocks seen are the loaded ones
     for _ in range(max(5, args.warmup // 2)):
         S.step()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.zero_()                     # 256 MiB write evicts L2 between steps
-        e0, e1, e2 = evs[i]
+        e0, e1, e2, ea = evs[i]
         e0.record()
         S.make_templates()
+        ea.record()
         S.normalise()
         e1.record()
         S.correlate(True)
@@ -273,8 +274,9 @@ def run_native(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(c) for a, _, c in evs]
-    conv_ms = [b.elapsed_time(c) for _, b, c in evs]
+    step_ms = [a.elapsed_time(c) for a, _, c, _ in evs]
+    conv_ms = [b.elapsed_time(c) for _, b, c, _ in evs]
+    tpl_ms = [a.elapsed_time(d) for a, _, _, d in evs]
     total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(total, op=dist.ReduceOp.MAX)
@@ -324,6 +326,7 @@ def run_native(args):
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel_ms": conv_mean},
             "front_ms": statistics.mean(a - b for a, b in zip(step_ms, conv_ms)),
+            "templates_ms": statistics.mean(tpl_ms),
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": wl.n * 4, "d2h_bytes_per_step": 4 * (1 + 4 * S.cap),
                     "candidates": n_cand},

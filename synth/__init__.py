@@ -107,9 +107,9 @@ class Workload:
         return Workload(**d)
 
 
-def _production_injections(seed: int, count: int = 8):
+def _production_injections(seed: int, count: int = 8, rmax: float = 4.0e6):
     rng = np.random.default_rng(seed + 1000)
-    r = rng.uniform(1.0e4, 4.0e6, count)
+    r = rng.uniform(1.0e4, rmax, count)
     z = rng.uniform(-200.0, 200.0, count)
     s = rng.uniform(6.0, 20.0, count)
     return tuple((float(a), float(b), float(c)) for a, b, c in zip(r, z, s))
@@ -125,6 +125,10 @@ WORKLOADS = {
     # (201 templates), taps padded to 256; segment length swept 1024-4096.
     "production": Workload("production", 1 << 23, 2, _production_injections(2),
                            -200, 200, 2, 256, 2048),
+    # The production search on a 2^20-sample series (201 x 2^20 plane, 0.84 GB):
+    # same kernels and launch shapes, small enough for hardware-counter captures.
+    "medium": Workload("medium", 1 << 20, 3, _production_injections(3, rmax=5.0e5),
+                       -200, 200, 2, 256, 2048),
     # A few-second oracle case that still spans several segments and a
     # ragged tail: 2^14 samples, 8192 bins, 1024-point segments of 960
     # useful bins (8.53 segments).
