@@ -37,7 +37,7 @@ import synth  # noqa: E402
 
 METRIC = "f-fdot plane points/s (2^23-sample series, zmax=200)"
 UNIT = "points/s"
-KERNELS_PER_STEP = 6   # templates 1, normalise 4, convolver 1
+KERNELS_PER_STEP = 7   # templates 2, normalise 4, convolver 1
 
 
 def parse():

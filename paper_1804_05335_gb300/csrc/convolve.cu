@@ -29,8 +29,9 @@
 // except for thread 0, handled separately.
 #include <algorithm>
 
-#include "dft.cuh"
+#include "conv_fft.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace fdas {
 
@@ -55,16 +56,15 @@ struct ConvArgs {
 };
 
 template <int L>
-struct ConvShape {
-    static constexpr int T = L / 16;
-    static constexpr int Q = L / 256;
-    static constexpr int X1S = 16 * (T + Q);
-    static constexpr int G = 16 * (Q + 1) + Q;
-    static constexpr int X2S = 16 * G;
-    static constexpr int BUFS = X1S > X2S ? X1S : X2S;
-    static constexpr int TW3 = 16 * (Q + 1);
-    static constexpr size_t smem_bytes = (size_t)(2 * BUFS + L + TW3) * sizeof(float2);
+struct ConvSmem {
+    using S = ConvShape<L>;
+    static constexpr int TW3 = 16 * (S::Q + 1);
+    // buf0 | buf1 | outb (L) | hbuf (L) | tw3
+    static constexpr size_t bytes = (size_t)(2 * S::BUFS + 2 * L + TW3) * sizeof(float2);
 };
+
+// polls of the template-row bulk copy before the kernel gives up
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, float v) {
     int idx = atomicAdd(A.count, 1);
@@ -80,22 +80,61 @@ __device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, fl
     }
 }
 
+// Template of item q inside a segment: bank row, plane row, conjugation.
+// Items of a symmetric grid pair +z with -z so that both use one bank row.
+__device__ __forceinline__ void item_row(const ConvArgs& A, int q, int& row, int& brow, int& cj) {
+    if (!A.sym) {
+        row = q; brow = q; cj = 0;
+        return;
+    }
+    if (A.zero) {
+        if (q == 0) { brow = 0; cj = 0; }
+        else { brow = (q + 1) >> 1; cj = (q & 1) ? 0 : 1; }
+    } else {
+        brow = q >> 1; cj = q & 1;
+    }
+    row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
+}
+
+// Powers of one pair of positions (j, j+1) given x[j], x[j+1], x[j+2].
+__device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
+    const float hs = 0.61685027506808491f;   // (pi/4)^2
+    const float dx0 = x01.x - x01.z, dy0 = x01.y - x01.w;
+    const float dx1 = x01.z - xn.x, dy1 = x01.w - xn.y;
+    return make_float4(fmaf(x01.x, x01.x, x01.y * x01.y), hs * fmaf(dx0, dx0, dy0 * dy0),
+                       fmaf(x01.z, x01.z, x01.w * x01.w), hs * fmaf(dx1, dx1, dy1 * dy1));
+}
+
 template <int L, bool FUSE>
-__global__ void __launch_bounds__(L / 16) conv_kernel(const ConvArgs A) {
+__global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const ConvArgs A) {
     using S = ConvShape<L>;
-    constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = 16 / Q;
+    constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
     extern __shared__ float4 smem4[];
     float2* buf0 = reinterpret_cast<float2*>(smem4);
     float2* buf1 = buf0 + BUFS;
     float2* outb = buf1 + BUFS;
-    float2* tw3 = outb + L;
+    float2* hbuf = outb + L;
+    float2* tw3 = hbuf + L;
+    __shared__ uint64_t hbar;
 
     const int t = threadIdx.x;
     const int a = t / Q, c = t % Q;
-    const int M = A.M, B = L - M;
+    const int M = A.M, B = L - M, NP = B / 2;
 
+    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
+    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
+    if (lo >= hi) return;
+    int64_t s = lo / A.K;
+    int q = (int)(lo - s * A.K);
+    int row, brow, cj;
+    item_row(A, q, row, brow, cj);
+
+    if (t == 0) {
+        mbar_init(&hbar, 1);
+        tma_load_1d(hbuf, A.bank + (size_t)brow * (L / 2), L * sizeof(float2), &hbar);
+    }
     // inverse pass-3' twiddles: tw3[k1*(Q+1) + n2] = exp(+i 2 pi n2 k1 / (L/16))
-    for (int idx = t; idx < S::TW3; idx += T) {
+    for (int idx = t; idx < ConvSmem<L>::TW3; idx += T) {
         int k1 = idx / (Q + 1), n2 = idx % (Q + 1);
         float sn, cs;
         sincospif(2.0f * (float)((n2 * k1) % (L / 16)) / (float)(L / 16), &sn, &cs);
@@ -113,94 +152,57 @@ __global__ void __launch_bounds__(L / 16) conv_kernel(const ConvArgs A) {
     const int tp = (a != 0) ? (16 - a) * Q + (Q - 1 - c) : (Q - c) % Q;
     __syncthreads();
 
-    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
-    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
     int64_t cur_seg = -1;
     int parity = 0;
+    uint32_t hphase = 0;
+    bool hpending = true;
     float2 Y[16];
     float2 v[16];
+    const float4* hb4 = reinterpret_cast<const float4*>(hbuf);
 
     for (int64_t w = lo; w < hi; ++w) {
-        const int64_t s = w / A.K;
-        const int q = (int)(w - s * A.K);
         if (s != cur_seg) {
-            // ---- forward FFT of segment s (once per segment) ----
+            // ---- forward FFT of segment s, once per segment ----
             cur_seg = s;
             const int64_t base = s * (int64_t)B - M / 2;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                int64_t pos = base + i * T + t;
+                const int64_t pos = base + i * T + t;
                 v[i] = (pos >= 0 && pos < A.nb) ? __ldg(&A.spec[pos]) : make_float2(0.f, 0.f);
             }
-            dft16<-1>(v);
-#pragma unroll
-            for (int k0 = 1; k0 < 16; ++k0) {
-                float sn, cs;
-                sincospif(2.0f * (float)(t * k0) / (float)L, &sn, &cs);
-                v[k0] = cmul(v[k0], make_float2(cs, -sn));
-            }
-            __syncthreads();   // previous users of buf0 / buf1 are done
-#pragma unroll
-            for (int i = 0; i < 16; ++i) buf0[i * (T + Q) + t] = v[i];
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = buf0[a * (T + Q) + i * Q + c];
-            dft16<-1>(v);
-#pragma unroll
-            for (int k1 = 1; k1 < 16; ++k1) {
-                float sn, cs;
-                sincospif(2.0f * (float)((c * k1) % (L / 16)) / (float)(L / 16), &sn, &cs);
-                v[k1] = cmul(v[k1], make_float2(cs, -sn));
-            }
-            float2* x2 = buf1 + a * G;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) x2[i * (Q + 1) + c] = v[i];
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = x2[(c + Q * (i / Q)) * (Q + 1) + (i % Q)];
-#pragma unroll
-            for (int s2 = 0; s2 < NS; ++s2) dftq<Q, -1>(v + s2 * Q);
+            forward_fft_d3<L>(v, buf0, buf1, t);
 #pragma unroll
             for (int i = 0; i < 16; ++i) Y[i] = v[i];
-            __syncthreads();   // buffers free for the template loop
+            __syncthreads();   // exchange buffers free again
             parity = 0;
         }
 
-        // ---- template row for item q ----
-        int row, brow, cj;
-        if (!A.sym) {
-            row = q; brow = q; cj = 0;
-        } else if (A.zero) {
-            if (q == 0) { brow = 0; cj = 0; }
-            else { brow = (q + 1) >> 1; cj = (q & 1) ? 0 : 1; }
-            row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
-        } else {
-            brow = q >> 1; cj = q & 1;
-            row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
+        // ---- multiply by the template spectrum staged in shared memory ----
+        bool tmo = false;
+        if (hpending) {
+            tmo = !mbar_wait_bounded(&hbar, hphase, kWaitLimit);
+            hphase ^= 1u;
+            hpending = false;
         }
-
-        // ---- multiply by the template spectrum (bank row via L2) ----
-        const float4* hb = A.bank + (size_t)brow * (L / 2);
         if (!cj) {
 #pragma unroll
             for (int ip = 0; ip < 8; ++ip) {
-                float4 h = __ldg(&hb[ip * T + t]);
+                const float4 h = hb4[ip * T + t];
                 v[2 * ip] = cmul(Y[2 * ip], make_float2(h.x, h.y));
                 v[2 * ip + 1] = cmul(Y[2 * ip + 1], make_float2(h.z, h.w));
             }
         } else if (t != 0) {
 #pragma unroll
             for (int ip = 0; ip < 8; ++ip) {
-                float4 h = __ldg(&hb[(7 - ip) * T + tp]);
+                const float4 h = hb4[(7 - ip) * T + tp];
                 v[2 * ip] = cmulc(Y[2 * ip], make_float2(h.z, h.w));
                 v[2 * ip + 1] = cmulc(Y[2 * ip + 1], make_float2(h.x, h.y));
             }
         } else {
-            const float2* hb2 = reinterpret_cast<const float2*>(hb);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int ii = (i < Q) ? ((Q - i) % Q) : (15 + Q - i);
-                v[i] = cmulc(Y[i], __ldg(&hb2[2 * ((ii >> 1) * T) + (ii & 1)]));
+                v[i] = cmulc(Y[i], hbuf[2 * ((ii >> 1) * T) + (ii & 1)]);
             }
         }
 
@@ -226,98 +228,136 @@ __global__ void __launch_bounds__(L / 16) conv_kernel(const ConvArgs A) {
 #pragma unroll
         for (int n1 = 0; n1 < 16; ++n1) v[n1] = cmul(v[n1], tw2[n1]);
         // ---- D2 -> D1 across the CTA ----
-        {
-            float2* x1 = parity ? buf1 : buf0;
+        float2* x1 = parity ? buf1 : buf0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) x1[a * (T + Q) + i * Q + c] = v[i];
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = x1[i * (T + Q) + t];
+        for (int i = 0; i < 16; ++i) x1[a * (T + Q) + i * Q + c] = v[i];
+        if (__syncthreads_or(tmo)) {
+            if (t == 0 && A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
+            break;
         }
+
+        // ---- next item; prefetch its template row if it changes ----
+        const int64_t s_next = (q + 1 == A.K) ? s + 1 : s;
+        const int q_next = (q + 1 == A.K) ? 0 : q + 1;
+        int row_n = 0, brow_n = brow, cj_n = 0;
+        if (w + 1 < hi) {
+            item_row(A, q_next, row_n, brow_n, cj_n);
+            if (brow_n != brow) {
+                if (t == 0) {
+                    fence_proxy_async();
+                    tma_load_1d(hbuf, A.bank + (size_t)brow_n * (L / 2), L * sizeof(float2), &hbar);
+                }
+                hpending = true;
+            }
+        }
+
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = x1[i * (T + Q) + t];
         // ---- inverse pass 1': radix 16 over k0 -> natural order ----
         dft16<1>(v);
 #pragma unroll
         for (int n0 = 0; n0 < 16; ++n0) outb[n0 * T + t] = v[n0];
         __syncthreads();
 
-        // ---- epilogue: powers of positions M/2 .. M/2+B (pairs of bins) ----
+        // ---- epilogue: powers of positions M/2 .. M/2+B, two bins per pair ----
         const int64_t r0 = s * (int64_t)B;
         float* prow = A.plane + (int64_t)row * A.row_stride;
-        const int NP = B / 2;
-        const float hs = 0.61685027506808491f;   // (pi/4)^2
-        for (int p = t; p < NP; p += T) {
-            const int j = M / 2 + 2 * p;
-            const float4 x01 = *reinterpret_cast<const float4*>(&outb[j]);
-            const float2 xn = outb[j + 2];
-            const float dx0 = x01.x - x01.z, dy0 = x01.y - x01.w;
-            const float dx1 = x01.z - xn.x, dy1 = x01.w - xn.y;
-            float p0 = fmaf(x01.x, x01.x, x01.y * x01.y);
-            float p1 = fmaf(x01.z, x01.z, x01.w * x01.w);
-            float h0 = hs * fmaf(dx0, dx0, dy0 * dy0);
-            float h1 = hs * fmaf(dx1, dx1, dy1 * dy1);
-            const int64_t r = r0 + 2 * p;
-            if (r + 2 < A.nb) {
-                if (A.interbin) {
-                    *reinterpret_cast<float4*>(prow + 2 * r) = make_float4(p0, h0, p1, h1);
-                } else {
-                    *reinterpret_cast<float2*>(prow + r) = make_float2(p0, p1);
+        const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
+        const float2* o2 = outb + M / 2 + 2;
+        float mx = 0.f;
+        if (r0 + B < A.nb) {
+            if (A.interbin) {
+                float4* dst = reinterpret_cast<float4*>(prow + 2 * r0);
+#pragma unroll 4
+                for (int p = t; p < NP; p += T) {
+                    const float4 pw = pair_powers(o4[p], o2[2 * p]);
+                    dst[p] = pw;
+                    if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
                 }
-            } else if (r < A.nb) {
-                // the last bins of the row: no r+1 beyond nb-1
-                if (r + 1 >= A.nb - 1) h1 = 0.f;
-                if (r >= A.nb - 1) h0 = 0.f;
-                if (A.interbin) {
-                    prow[2 * r] = p0;
-                    prow[2 * r + 1] = h0;
-                    if (r + 1 < A.nb) { prow[2 * r + 2] = p1; prow[2 * r + 3] = h1; }
-                } else {
-                    prow[r] = p0;
-                    if (r + 1 < A.nb) prow[r + 1] = p1;
-                }
-                if (r + 1 >= A.nb) { p1 = 0.f; h1 = 0.f; }
             } else {
-                p0 = p1 = h0 = h1 = 0.f;
+                float2* dst = reinterpret_cast<float2*>(prow + r0);
+#pragma unroll 4
+                for (int p = t; p < NP; p += T) {
+                    const float4 x = o4[p];
+                    const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
+                    dst[p] = pw;
+                    if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
+                }
             }
-            if constexpr (FUSE) {
-                float m = fmaxf(fmaxf(p0, p1), fmaxf(h0, h1));
-                if (m > A.thr) {
+        } else {
+            // segment reaching the end of the spectrum: per-bin checks
+            for (int p = t; p < NP; p += T) {
+                const int64_t r = r0 + 2 * p;
+                if (r >= A.nb) break;
+                float4 pw = pair_powers(o4[p], o2[2 * p]);
+                if (r + 1 >= A.nb - 1) pw.w = 0.f;       // no bin r+2
+                if (r >= A.nb - 1) pw.y = 0.f;           // no bin r+1
+                if (r + 1 >= A.nb) { pw.z = 0.f; pw.w = 0.f; }
+                if (A.interbin) {
+                    prow[2 * r] = pw.x;
+                    prow[2 * r + 1] = pw.y;
+                    if (r + 1 < A.nb) { prow[2 * r + 2] = pw.z; prow[2 * r + 3] = pw.w; }
+                } else {
+                    prow[r] = pw.x;
+                    if (r + 1 < A.nb) prow[r + 1] = pw.z;
+                    pw.y = 0.f;
+                    pw.w = 0.f;
+                }
+                if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
+            }
+        }
+        if constexpr (FUSE) {
+            if (mx > A.thr) {
+                // rare: rescan this thread's pairs and emit each crossing
+                for (int p = t; p < NP; p += T) {
+                    const int64_t r = r0 + 2 * p;
+                    if (r >= A.nb) break;
+                    float4 pw = pair_powers(o4[p], o2[2 * p]);
+                    if (r + 1 >= A.nb - 1) pw.w = 0.f;
+                    if (r >= A.nb - 1) pw.y = 0.f;
+                    if (r + 1 >= A.nb) { pw.z = 0.f; pw.w = 0.f; }
                     if (A.interbin) {
-                        if (p0 > A.thr) emit(A, row, 2 * r, p0);
-                        if (h0 > A.thr) emit(A, row, 2 * r + 1, h0);
-                        if (p1 > A.thr) emit(A, row, 2 * r + 2, p1);
-                        if (h1 > A.thr) emit(A, row, 2 * r + 3, h1);
+                        if (pw.x > A.thr) emit(A, row, 2 * r, pw.x);
+                        if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y);
+                        if (pw.z > A.thr) emit(A, row, 2 * r + 2, pw.z);
+                        if (pw.w > A.thr) emit(A, row, 2 * r + 3, pw.w);
                     } else {
-                        if (p0 > A.thr) emit(A, row, r, p0);
-                        if (p1 > A.thr) emit(A, row, r + 1, p1);
+                        if (pw.x > A.thr) emit(A, row, r, pw.x);
+                        if (pw.z > A.thr) emit(A, row, r + 1, pw.z);
                     }
                 }
             }
         }
         parity ^= 1;
+        s = s_next;
+        q = q_next;
+        row = row_n;
+        brow = brow_n;
+        cj = cj_n;
     }
 }
 
 template <int L, bool FUSE>
 static int launch_one(const ConvArgs& args, cudaStream_t st) {
     using S = ConvShape<L>;
+    constexpr size_t smem = ConvSmem<L>::bytes;
     static int grid = 0;
     if (grid == 0) {
         cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::smem_bytes);
+                                             (int)smem);
         if (e != cudaSuccess) return FDAS_E_CUDA;
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE>, S::T,
-                                                          S::smem_bytes) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE>, S::T, smem) != cudaSuccess)
             return FDAS_E_CUDA;
         if (per_sm < 1) return FDAS_E_UNSUPPORTED;
         grid = sms * per_sm;
     }
     int64_t g = std::min<int64_t>(grid, std::max<int64_t>(1, args.items));
-    conv_kernel<L, FUSE><<<(unsigned)g, S::T, S::smem_bytes, st>>>(args);
+    conv_kernel<L, FUSE><<<(unsigned)g, S::T, smem, st>>>(args);
     return cuda_status(cudaGetLastError());
 }
 

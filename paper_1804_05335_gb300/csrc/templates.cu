@@ -1,5 +1,8 @@
 // fdas_make_templates: FP64 template responses (Fresnel integrals) and their
-// L-point spectra, stored FP32 in the convolver's digit-reversed order.
+// L-point spectra, stored FP32 in the convolver's digit-reversed order.  The
+// spectra come from the convolver's own forward FFT, so no reordering is
+// ever needed (Section 4.2: the templates must be transformed by the same
+// algorithm as the segments).
 //
 // Response of a unit constant-fdot signal at offset d from its
 // mid-observation bin (Section 2, Eqs. 22-23):
@@ -14,10 +17,12 @@
 // is the Laplace continued fraction of erfc (its tail integral).  Because
 // pi X^2/2 = pi q^2/z and pi Y^2/2 - pi q^2/z = -2 pi d (mod 2 pi), the large
 // quadratic phases cancel analytically and only bounded phases are ever
-// evaluated.  For |x| < 2 the power series of F is used.  z < 0 follows from
+// evaluated.  For |x| < 2 the power series of F is used (FP64); E is
+// evaluated in FP32 (bounded and smooth, see fresnel_tail_e).  z < 0 follows from
 // R_{-z}(d) = e^{-i 2 pi d} conj(R_z(d)).
 #include <math.h>
 
+#include "conv_fft.cuh"
 #include "internal.h"
 
 namespace fdas {
@@ -29,10 +34,6 @@ __device__ __forceinline__ cd cadd(cd a, cd b) { return {a.x + b.x, a.y + b.y}; 
 __device__ __forceinline__ cd csub(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
 __device__ __forceinline__ cd cmuld(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 __device__ __forceinline__ cd cscale(cd a, double s) { return {a.x * s, a.y * s}; }
-__device__ __forceinline__ cd cinv(cd a) {
-    double n = a.x * a.x + a.y * a.y;
-    return {a.x / n, -a.y / n};
-}
 // exp(i pi t)
 __device__ __forceinline__ cd expipi(double t) {
     double s, c;
@@ -40,56 +41,83 @@ __device__ __forceinline__ cd expipi(double t) {
     return {c, s};
 }
 
-// F(x) = int_0^x e^{i pi t^2/2} dt for |x| < 2 by its power series
-//   sum_n (i pi x^2/2)^n / n! * x / (2n+1).
+// Power series of the Fresnel integrals in powers of x^4, coefficients from
+// their definitions:  C(x) = x sum_n (-1)^n (pi/2)^{2n} x^{4n} / ((2n)! (4n+1)),
+//                     S(x) = x^3 sum_n (-1)^n (pi/2)^{2n+1} x^{4n} / ((2n+1)! (4n+3)).
+constexpr double kHalfPi = 1.57079632679489662;
+constexpr double cfact(int k) { return k <= 1 ? 1.0 : k * cfact(k - 1); }
+constexpr double cpow(double b, int e) { return e == 0 ? 1.0 : b * cpow(b, e - 1); }
+constexpr double ser_c(int n) {
+    return (n % 2 ? -1.0 : 1.0) * cpow(kHalfPi, 2 * n) / (cfact(2 * n) * (4 * n + 1));
+}
+constexpr double ser_s(int n) {
+    return (n % 2 ? -1.0 : 1.0) * cpow(kHalfPi, 2 * n + 1) / (cfact(2 * n + 1) * (4 * n + 3));
+}
+constexpr int kSerTerms = 24;   // |x| < 2: the last term is below 1e-22
+__constant__ double kSerC[kSerTerms] = {
+    ser_c(0), ser_c(1), ser_c(2), ser_c(3), ser_c(4), ser_c(5), ser_c(6), ser_c(7),
+    ser_c(8), ser_c(9), ser_c(10), ser_c(11), ser_c(12), ser_c(13), ser_c(14), ser_c(15),
+    ser_c(16), ser_c(17), ser_c(18), ser_c(19), ser_c(20), ser_c(21), ser_c(22), ser_c(23)};
+__constant__ double kSerS[kSerTerms] = {
+    ser_s(0), ser_s(1), ser_s(2), ser_s(3), ser_s(4), ser_s(5), ser_s(6), ser_s(7),
+    ser_s(8), ser_s(9), ser_s(10), ser_s(11), ser_s(12), ser_s(13), ser_s(14), ser_s(15),
+    ser_s(16), ser_s(17), ser_s(18), ser_s(19), ser_s(20), ser_s(21), ser_s(22), ser_s(23)};
+
+// F(x) = C(x) + i S(x) for |x| < 2 (FP64 Horner in x^4).
 __device__ cd fresnel_series(double x) {
-    const double a = M_PI * x * x * 0.5;
-    cd p = {1.0, 0.0};
-    cd s = {x, 0.0};
-    for (int n = 1; n < 46; ++n) {
-        p = cscale(cmuld(p, cd{0.0, a}), 1.0 / n);
-        s = cadd(s, cscale(p, x / (2 * n + 1)));
+    const double x2 = x * x, x4 = x2 * x2;
+    double c = kSerC[kSerTerms - 1], s = kSerS[kSerTerms - 1];
+#pragma unroll
+    for (int n = kSerTerms - 2; n >= 0; --n) {
+        c = fma(c, x4, kSerC[n]);
+        s = fma(s, x4, kSerS[n]);
     }
-    return s;
+    return {x * c, x * x2 * s};
 }
 
-// E(x), x >= 2: the continued fraction evaluated from the tail with a term
-// count that gives ~1e-16 for every x >= 2.
-__device__ cd fresnel_tail_e(double x) {
-    const double sp2 = 0.88622692545275801;   // sqrt(pi)/2
-    cd w = {sp2 * x, -sp2 * x};
-    int N = x < 2.5 ? 48 : x < 3.2 ? 32 : x < 4.0 ? 24 : x < 5.0 ? 16 : x < 6.0 ? 12 : x < 8.0 ? 10 : 8;
-    cd f = w;
-    for (int n = N; n >= 1; --n) f = cadd(w, cscale(cinv(f), 0.5 * n));
-    const double k = 0.28209479177387814;     // 1/(2 sqrt(pi))
-    return cmuld(cd{k, k}, cinv(f));
+// E(x), x >= 2, by the continued fraction evaluated from its tail, in FP32:
+// |E| <= 0.16 and varies slowly, and the FP32 evaluation is within 3e-7 of
+// it relative, below the FP32 rounding of the stored taps.  Only the
+// quadratic phases, which grow with |z|, need FP64.
+__device__ cd fresnel_tail_e(double xd) {
+    const float x = (float)xd;
+    const float sp2 = 0.88622692545275801f;   // sqrt(pi)/2
+    const float wx = sp2 * x, wy = -sp2 * x;
+    const int N = x < 2.5f ? 48 : x < 3.2f ? 32 : x < 4.0f ? 24 : x < 5.0f ? 16
+                : x < 6.0f ? 12 : x < 8.0f ? 10 : 8;
+    float fx = wx, fy = wy;
+    for (int n = N; n >= 1; --n) {
+        const float h = (0.5f * (float)n) / fmaf(fx, fx, fy * fy);
+        fx = fmaf(h, fx, wx);                    // w + (n/2) conj(f)/|f|^2
+        fy = fmaf(-h, fy, wy);
+    }
+    const float inv = 1.0f / fmaf(fx, fx, fy * fy);
+    const float rx = fx * inv, ry = -fy * inv;
+    const float k = 0.28209479177387814f;     // 1/(2 sqrt(pi)); E = k (1+i) / f
+    return {(double)(k * (rx - ry)), (double)(k * (rx + ry))};
 }
 
-// e^{-i pi q^2/z} F(x) for x = X (tag 0) or x = Y (tag 1), using the phase
-// identities above for |x| >= 2.
-__device__ cd phased_f(double x, int isY, double q2z, double d) {
-    double ax = fabs(x);
-    if (ax < 2.0) {
-        cd f = fresnel_series(x);
-        return cmuld(expipi(-q2z), f);
-    }
-    double sg = x < 0 ? -1.0 : 1.0;
+// e^{-i pi q^2/z} F(x) for x = X (isY = 0) or x = Y (isY = 1), using the
+// phase identities above for |x| >= 2.  eyd = e^{-i 2 pi d}.
+__device__ cd phased_f(double x, int isY, cd ph, cd eyd) {
+    const double ax = fabs(x);
+    if (ax < 2.0) return cmuld(ph, fresnel_series(x));
+    const double sg = x < 0 ? -1.0 : 1.0;
     cd e = fresnel_tail_e(ax);
-    if (isY) e = cmuld(e, expipi(-2.0 * d));        // e^{-i pi q^2/z} e^{i pi Y^2/2} = e^{-i 2 pi d}
-    cd half = cmuld(expipi(-q2z), cd{0.5, 0.5});
+    if (isY) e = cmuld(e, eyd);
+    const cd half = cmuld(ph, cd{0.5, 0.5});
     return cscale(csub(half, e), sg);
 }
 
 // R_z(d) in FP64 for integer-or-real d, z > 0.
 __device__ cd response_pos(double z, double d) {
-    double q = -(d + 0.5 * z);
-    double s = sqrt(2.0 * z);
-    double X = s * q / z;
-    double Y = s * (1.0 + q / z);
-    double q2z = q * q / z;
-    cd fy = phased_f(Y, 1, q2z, d);
-    cd fx = phased_f(X, 0, q2z, d);
-    cd r = csub(fy, fx);
+    const double q = -(d + 0.5 * z);
+    const double s = sqrt(2.0 * z);
+    const double X = s * q / z;
+    const double Y = s * (1.0 + q / z);
+    const cd ph = expipi(-(q * q / z));
+    const cd eyd = (d == floor(d)) ? cd{1.0, 0.0} : expipi(-2.0 * d);
+    const cd r = csub(phased_f(Y, 1, ph, eyd), phased_f(X, 0, ph, eyd));
     return cscale(r, 1.0 / s);
 }
 
@@ -107,74 +135,88 @@ __device__ cd response(double z, double d) {
     return cmuld(expipi(-2.0 * d), r);
 }
 
-// Storage slot of frequency k in the convolver's order (see fdas.h).
-__device__ __forceinline__ int bank_slot(int k, int L) {
-    const int Q = L / 256, T = L / 16;
-    int a = k & 15, k1 = (k >> 4) & 15, c2 = k >> 8;
-    int c1 = k1 % Q, s2 = k1 / Q;
-    int t = a * Q + c1, i = s2 * Q + c2;
-    return 2 * ((i >> 1) * T + t) + (i & 1);
-}
+constexpr int kTapThreads = 128;
 
-constexpr int kTplThreads = 512;
-constexpr int kMaxTaps = 2 * 1024 + 1;
-
-// One CTA per bank row.  Phase 1: taps conj(R_z(d)) in FP64, rounded to
-// FP32 in shared memory.  Phase 2: H[k] = (1/L) sum_d conj(R(d)) e^{+i 2 pi d k/L}
-// (= FFT_L of the circularly placed kernel g[j] = conj(R(-j)), over 1/L),
-// accumulated in FP32 with Kahan compensation against a twiddle table.
-__global__ void __launch_bounds__(kTplThreads) templates_kernel(int L, int zfirst, int zstep,
-                                                                float2* __restrict__ bank) {
-    extern __shared__ float2 tsm[];
-    float2* tw = tsm;            // L entries: e^{+i 2 pi m / L}
-    float2* taps = tsm + L;      // 2h+1 entries
-    const int b = blockIdx.x;
+// Kernel 1: one thread per (bank row b, offset d), d = -h..h.  Writes the
+// FIR kernel taps g[j] = conj(R_z(-j)) / L for j = -d to the start of bank
+// row b as tap index j + h (float2), where the row-b CTA of kernel 2 reads
+// them before it overwrites the row.
+__global__ void __launch_bounds__(kTapThreads) template_taps_kernel(int L, int zfirst, int zstep,
+                                                                    int width, int rows,
+                                                                    float2* __restrict__ bank) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= rows * width) return;
+    const int b = gid / width, idx = gid - b * width;
     const int z = zfirst + b * zstep;
     const int az = z < 0 ? -z : z;
     const int h = (az + 1) / 2 + 8;
-    for (int d = -h + (int)threadIdx.x; d <= h; d += blockDim.x) {
-        cd r = response((double)z, (double)d);
-        taps[d + h] = make_float2((float)r.x, (float)-r.y);
+    if (idx > 2 * h) return;
+    const int j = idx - h;                       // tap position (circular index j mod L)
+    const cd r = response((double)z, (double)(-j));
+    const double s = 1.0 / (double)L;
+    bank[(size_t)b * L + idx] = make_float2((float)(r.x * s), (float)(-r.y * s));
+}
+
+// Kernel 2: one CTA of L/16 threads per bank row: gather the circularly
+// placed kernel g (D1 distribution), forward FFT with the convolver's own
+// permutation-free transform, store the digit-reversed spectrum in place.
+template <int L>
+__global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zstep,
+                                                              float2* __restrict__ bank) {
+    using S = ConvShape<L>;
+    constexpr int T = S::T;
+    extern __shared__ float4 tsm4[];
+    float2* buf0 = reinterpret_cast<float2*>(tsm4);
+    float2* buf1 = buf0 + S::BUFS;
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int z = zfirst + b * zstep;
+    const int az = z < 0 ? -z : z;
+    const int h = (az + 1) / 2 + 8;
+    float2* row = bank + (size_t)b * L;
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int p = i * T + t;
+        const int j = p <= h ? p : p - L;        // circular tap position
+        v[i] = (j >= -h && j <= h) ? row[j + h] : make_float2(0.f, 0.f);
     }
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        float s, c;
-        sincospif(2.0f * (float)m / (float)L, &s, &c);
-        tw[m] = make_float2(c, s);
+    __syncthreads();   // every tap is read before the row is overwritten
+    forward_fft_d3<L>(v, buf0, buf1, t);
+    float4* row4 = reinterpret_cast<float4*>(row);
+#pragma unroll
+    for (int ip = 0; ip < 8; ++ip)
+        row4[ip * T + t] = make_float4(v[2 * ip].x, v[2 * ip].y, v[2 * ip + 1].x, v[2 * ip + 1].y);
+}
+
+template <int L>
+static int launch_fft(int rows, int zfirst, int zstep, float2* bank, cudaStream_t st) {
+    constexpr size_t sm = 2 * ConvShape<L>::BUFS * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(template_fft_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess)
+            return FDAS_E_CUDA;
+        attr = true;
     }
-    __syncthreads();
-    const float invL = 1.0f / (float)L;
-    const int mask = L - 1;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
-        float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-        for (int d = -h; d <= h; ++d) {
-            float2 g = taps[d + h];
-            float2 w = tw[((d & mask) * k) & mask];
-            float tx = fmaf(g.x, w.x, -g.y * w.y);
-            float ty = fmaf(g.x, w.y, g.y * w.x);
-            float yx = tx - cx, yy = ty - cy;
-            float nx = sx + yx, ny = sy + yy;
-            cx = (nx - sx) - yx;
-            cy = (ny - sy) - yy;
-            sx = nx;
-            sy = ny;
-        }
-        bank[(size_t)b * L + bank_slot(k, L)] = make_float2(sx * invL, sy * invL);
-    }
+    template_fft_kernel<L><<<rows, L / 16, sm, st>>>(zfirst, zstep, bank);
+    return cuda_status(cudaGetLastError());
 }
 
 int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st) {
-    if (g.hmax * 2 + 1 > kMaxTaps) return FDAS_E_UNSUPPORTED;
-    size_t sm = (size_t)(p->L + 2 * g.hmax + 1) * sizeof(float2);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(templates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((4096 + kMaxTaps) * sizeof(float2)));
-        if (e != cudaSuccess) return FDAS_E_CUDA;
-        attr_done = true;
+    const int width = 2 * g.hmax + 1;
+    if (width > p->L) return FDAS_E_UNSUPPORTED;
+    const int zfirst = p->zmin + g.j0 * p->zstep;
+    const int total = g.Kb * width;
+    template_taps_kernel<<<(total + kTapThreads - 1) / kTapThreads, kTapThreads, 0, st>>>(
+        p->L, zfirst, p->zstep, width, g.Kb, bank);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return FDAS_E_CUDA;
+    switch (p->L) {
+        case 1024: return launch_fft<1024>(g.Kb, zfirst, p->zstep, bank, st);
+        case 2048: return launch_fft<2048>(g.Kb, zfirst, p->zstep, bank, st);
+        case 4096: return launch_fft<4096>(g.Kb, zfirst, p->zstep, bank, st);
+        default: return FDAS_E_INVAL;
     }
-    int zfirst = p->zmin + g.j0 * p->zstep;
-    templates_kernel<<<g.Kb, kTplThreads, sm, st>>>(p->L, zfirst, p->zstep, bank);
-    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace fdas
