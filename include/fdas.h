@@ -111,6 +111,9 @@ int32_t fdas_num_templates(const fdas_params *p);
  * the number of negative z in a symmetric grid and 0 otherwise. */
 int32_t fdas_bank_rows(const fdas_params *p);
 
+/* Size of the template bank in floats: fdas_bank_rows(p) * (L + 16) * 2. */
+int64_t fdas_bank_floats(const fdas_params *p);
+
 /* Number of overlap-save segments for nb bins: ceil(nb / (L - M)). */
 int64_t fdas_num_segments(const fdas_params *p, int64_t nb);
 
@@ -127,11 +130,16 @@ int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
  * for d = -h..h, the FIR kernel g[j] = conj(R_z(-j)) is placed circularly
  * (j >= 0 at the start, j < 0 at the end, zeros between) and
  *   H_z[k] = (1/L) sum_j g[j] exp(-i 2 pi j k / L),  k = 0..L-1
- * is stored in FP32 in the convolver's digit-reversed order:
- *   bank[(b*L + s)*2 + {0,1}] = H_z[k(s)] (re, im), slot s = 0..L-1,
+ * is stored in FP32 in the convolver's digit-reversed order.  A bank row is
+ * L + 16 complex values (fdas_bank_floats gives the total size):
+ *   bank[(b*(L+16) + s)*2 + {0,1}] = H_z[k(s)] (re, im), slot s = 0..L-1,
  *   with Q = L/256, T = L/16, s = 2*(ip*T + t) + e, i = 2*ip + e,
- *   t = a*Q + c1, i = s2*Q + c2  ->  k(s) = a + 16*(c1 + Q*s2) + 256*c2.
- * bank: (device) fdas_bank_rows(p) * L complex, 16-byte aligned; written.
+ *   t = a*Q + c1, i = s2*Q + c2  ->  k(s) = a + 16*(c1 + Q*s2) + 256*c2;
+ *   slots L..L+15 repeat, for the 16 frequencies of t = 0, the values at
+ *   -k mod L: complex L + 2*j + 1 - e holds H_z[-k(s)] of slot
+ *   s = 2*(7-j)*T + e (j = 0..7, e = 0..1), which lets conjugated templates
+ *   be read with one access pattern for every thread.
+ * bank: (device) fdas_bank_floats(p) floats, 16-byte aligned; written.
  * Errors: FDAS_E_INVAL for bad params or NULL bank.
  */
 int fdas_make_templates(const fdas_params *p, float *bank, void *stream);

@@ -14,7 +14,7 @@ import re
 __all__ = [
     "FdasError", "fdas_params", "fdas_cand", "fdas_fused_threshold", "load_library", "lib_path",
     "params", "fdas_strerror", "fdas_version", "fdas_half_width", "fdas_num_templates",
-    "fdas_bank_rows", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
+    "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_correlate", "fdas_threshold",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
     "FDAS_OK", "FDAS_E_INVAL", "FDAS_E_CUDA", "FDAS_E_OVERFLOW", "FDAS_E_TIMEOUT",
@@ -80,6 +80,7 @@ def load_library():
         "fdas_num_templates": (c_i32, [P(fdas_params)]),
         "fdas_bank_rows": (c_i32, [P(fdas_params)]),
         "fdas_num_segments": (c_i64, [P(fdas_params), c_i64]),
+        "fdas_bank_floats": (c_i64, [P(fdas_params)]),
         "fdas_plane_width": (c_i64, [P(fdas_params), c_i64]),
         "fdas_make_templates": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
         "fdas_normalise_workspace_bytes": (c_sz, [c_i64]),
@@ -158,6 +159,10 @@ def fdas_bank_rows(p: fdas_params) -> int:
     return _check(load_library().fdas_bank_rows(ctypes.byref(p)), "fdas_bank_rows")
 
 
+def fdas_bank_floats(p: fdas_params) -> int:
+    return _check(load_library().fdas_bank_floats(ctypes.byref(p)), "fdas_bank_floats")
+
+
 def fdas_num_segments(p: fdas_params, nb: int) -> int:
     return _check(load_library().fdas_num_segments(ctypes.byref(p), int(nb)), "fdas_num_segments")
 
@@ -167,7 +172,7 @@ def fdas_plane_width(p: fdas_params, nb: int) -> int:
 
 
 def fdas_make_templates(p: fdas_params, bank, stream=None) -> None:
-    """bank: device float32 tensor of fdas_bank_rows(p) * L * 2 elements."""
+    """bank: device float32 tensor of fdas_bank_floats(p) elements."""
     _check(load_library().fdas_make_templates(ctypes.byref(p), _ptr(bank), _stream(stream)),
            "fdas_make_templates")
 

@@ -72,6 +72,12 @@ int32_t fdas_bank_rows(const fdas_params* p) {
     return rc == FDAS_OK ? g.Kb : rc;
 }
 
+int64_t fdas_bank_floats(const fdas_params* p) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    return rc == FDAS_OK ? (int64_t)g.Kb * (p->L + 16) * 2 : rc;
+}
+
 int64_t fdas_num_segments(const fdas_params* p, int64_t nb) {
     Grid g;
     if (make_grid(p, &g) != FDAS_OK || nb < 1) return FDAS_E_INVAL;

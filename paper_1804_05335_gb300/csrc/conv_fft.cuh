@@ -28,7 +28,17 @@ struct ConvShape {
     static constexpr int G = 16 * (Q + 1) + Q;
     static constexpr int X2S = 16 * G;
     static constexpr int BUFS = X1S > X2S ? X1S : X2S;   // float2 per exchange buffer
+    // bank row: L digit-reversed slots, then 16 slots holding H[-k] for the
+    // frequencies of thread 0 (see thread0_mirror), in float2
+    static constexpr int ROW = L + 16;
 };
+
+// Register of thread 0 (D3) that holds -k for the frequency k of its register
+// i: its 16 frequencies are closed under negation (k = 256 c2 + 16 Q s).
+template <int Q>
+__host__ __device__ constexpr int thread0_mirror(int i) {
+    return i < Q ? (Q - i) % Q : 15 + Q - i;
+}
 
 // exp(-i 2 pi e / N), 0 <= e < N, N a power of two
 __device__ __forceinline__ float2 fwd_twiddle(int e, int N) {

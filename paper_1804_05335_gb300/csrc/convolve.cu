@@ -59,8 +59,8 @@ template <int L>
 struct ConvSmem {
     using S = ConvShape<L>;
     static constexpr int TW3 = 16 * (S::Q + 1);
-    // buf0 | buf1 | outb (L) | hbuf (L) | tw3
-    static constexpr size_t bytes = (size_t)(2 * S::BUFS + 2 * L + TW3) * sizeof(float2);
+    // buf0 | buf1 | outb (L) | hbuf (bank row) | tw3
+    static constexpr size_t bytes = (size_t)(2 * S::BUFS + L + S::ROW + TW3) * sizeof(float2);
 };
 
 // polls of the template-row bulk copy before the kernel gives up
@@ -106,7 +106,7 @@ __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
 }
 
 template <int L, bool FUSE>
-__global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const ConvArgs A) {
+__global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const ConvArgs A) {
     using S = ConvShape<L>;
     constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
     extern __shared__ float4 smem4[];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
     float2* buf1 = buf0 + BUFS;
     float2* outb = buf1 + BUFS;
     float2* hbuf = outb + L;
-    float2* tw3 = hbuf + L;
+    float2* tw3 = hbuf + S::ROW;
     __shared__ uint64_t hbar;
 
     const int t = threadIdx.x;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
 
     if (t == 0) {
         mbar_init(&hbar, 1);
-        tma_load_1d(hbuf, A.bank + (size_t)brow * (L / 2), L * sizeof(float2), &hbar);
+        tma_load_1d(hbuf, A.bank + (size_t)brow * (S::ROW / 2), S::ROW * sizeof(float2), &hbar);
     }
     // inverse pass-3' twiddles: tw3[k1*(Q+1) + n2] = exp(+i 2 pi n2 k1 / (L/16))
     for (int idx = t; idx < ConvSmem<L>::TW3; idx += T) {
@@ -148,8 +148,12 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
         sincospif(2.0f * (float)(((n1 * Q + c) * a) % L) / (float)L, &sn, &cs);
         tw2[n1] = make_float2(cs, sn);
     }
-    // partner thread holding -k for the conjugate (z < 0) templates
+    // conjugate (z < 0) templates read H[-k]: float4 pair ip of this thread
+    // sits at hbase - ip*hstep, halves swapped (partner thread, reversed
+    // registers); thread 0 reads the mirror slots at the end of the row.
     const int tp = (a != 0) ? (16 - a) * Q + (Q - 1 - c) : (Q - c) % Q;
+    const int hbase = (t == 0) ? L / 2 + 7 : 7 * T + tp;
+    const int hstep = (t == 0) ? 1 : T;
     __syncthreads();
 
     int64_t cur_seg = -1;
@@ -191,18 +195,12 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
                 v[2 * ip] = cmul(Y[2 * ip], make_float2(h.x, h.y));
                 v[2 * ip + 1] = cmul(Y[2 * ip + 1], make_float2(h.z, h.w));
             }
-        } else if (t != 0) {
-#pragma unroll
-            for (int ip = 0; ip < 8; ++ip) {
-                const float4 h = hb4[(7 - ip) * T + tp];
-                v[2 * ip] = cmulc(Y[2 * ip], make_float2(h.z, h.w));
-                v[2 * ip + 1] = cmulc(Y[2 * ip + 1], make_float2(h.x, h.y));
-            }
         } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int ii = (i < Q) ? ((Q - i) % Q) : (15 + Q - i);
-                v[i] = cmulc(Y[i], hbuf[2 * ((ii >> 1) * T) + (ii & 1)]);
+            for (int ip = 0; ip < 8; ++ip) {
+                const float4 h = hb4[hbase - ip * hstep];
+                v[2 * ip] = cmulc(Y[2 * ip], make_float2(h.z, h.w));
+                v[2 * ip + 1] = cmulc(Y[2 * ip + 1], make_float2(h.x, h.y));
             }
         }
 
@@ -245,7 +243,8 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
             if (brow_n != brow) {
                 if (t == 0) {
                     fence_proxy_async();
-                    tma_load_1d(hbuf, A.bank + (size_t)brow_n * (L / 2), L * sizeof(float2), &hbar);
+                    tma_load_1d(hbuf, A.bank + (size_t)brow_n * (S::ROW / 2), S::ROW * sizeof(float2),
+                                &hbar);
                 }
                 hpending = true;
             }
@@ -266,22 +265,29 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 3 : 1) conv_kernel(const C
         const float2* o2 = outb + M / 2 + 2;
         float mx = 0.f;
         if (r0 + B < A.nb) {
+            constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
             if (A.interbin) {
                 float4* dst = reinterpret_cast<float4*>(prow + 2 * r0);
-#pragma unroll 4
-                for (int p = t; p < NP; p += T) {
-                    const float4 pw = pair_powers(o4[p], o2[2 * p]);
-                    dst[p] = pw;
-                    if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
+#pragma unroll
+                for (int u = 0; u < UMAX; ++u) {
+                    const int p = t + u * T;
+                    if (p < NP) {
+                        const float4 pw = pair_powers(o4[p], o2[2 * p]);
+                        __stcs(dst + p, pw);
+                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
+                    }
                 }
             } else {
                 float2* dst = reinterpret_cast<float2*>(prow + r0);
-#pragma unroll 4
-                for (int p = t; p < NP; p += T) {
-                    const float4 x = o4[p];
-                    const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
-                    dst[p] = pw;
-                    if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
+#pragma unroll
+                for (int u = 0; u < UMAX; ++u) {
+                    const int p = t + u * T;
+                    if (p < NP) {
+                        const float4 x = o4[p];
+                        const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
+                        __stcs(dst + p, pw);
+                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
+                    }
                 }
             }
         } else {

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kTapThreads) template_taps_kernel(int L, int z
     const int j = idx - h;                       // tap position (circular index j mod L)
     const cd r = response((double)z, (double)(-j));
     const double s = 1.0 / (double)L;
-    bank[(size_t)b * L + idx] = make_float2((float)(r.x * s), (float)(-r.y * s));
+    bank[(size_t)b * (L + 16) + idx] = make_float2((float)(r.x * s), (float)(-r.y * s));
 }
 
 // Kernel 2: one CTA of L/16 threads per bank row: gather the circularly
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zs
     const int z = zfirst + b * zstep;
     const int az = z < 0 ? -z : z;
     const int h = (az + 1) / 2 + 8;
-    float2* row = bank + (size_t)b * L;
+    float2* row = bank + (size_t)b * S::ROW;
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -186,6 +186,17 @@ __global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zs
 #pragma unroll
     for (int ip = 0; ip < 8; ++ip)
         row4[ip * T + t] = make_float4(v[2 * ip].x, v[2 * ip].y, v[2 * ip + 1].x, v[2 * ip + 1].y);
+    if (t == 0) {
+        // mirror slots: float4 L/2 + j holds (H[-k(2ip+1)], H[-k(2ip)]) of thread 0, ip = 7 - j,
+        // so that the conjugate-template read of thread 0 has the same form as everyone's
+        constexpr int Q = S::Q;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int ip = 7 - j;
+            const float2 hi = v[thread0_mirror<Q>(2 * ip + 1)], lo = v[thread0_mirror<Q>(2 * ip)];
+            row4[L / 2 + j] = make_float4(hi.x, hi.y, lo.x, lo.y);
+        }
+    }
 }
 
 template <int L>
@@ -204,7 +215,7 @@ static int launch_fft(int rows, int zfirst, int zstep, float2* bank, cudaStream_
 
 int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st) {
     const int width = 2 * g.hmax + 1;
-    if (width > p->L) return FDAS_E_UNSUPPORTED;
+    if (width > p->L + 16) return FDAS_E_UNSUPPORTED;
     const int zfirst = p->zmin + g.j0 * p->zstep;
     const int total = g.Kb * width;
     template_taps_kernel<<<(total + kTapThreads - 1) / kTapThreads, kTapThreads, 0, st>>>(

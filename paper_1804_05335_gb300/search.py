@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (fdas_bank_rows, fdas_correlate, fdas_fused_threshold, fdas_make_templates,
+from . import (fdas_bank_floats, fdas_bank_rows, fdas_correlate, fdas_fused_threshold, fdas_make_templates,
                fdas_normalise, fdas_normalise_workspace_bytes, fdas_num_segments,
                fdas_num_templates, fdas_plane_width, fdas_threshold, params)
 
@@ -38,7 +38,7 @@ class Search:
         self.spec = torch.empty(self.nb, dtype=torch.complex64, device=dev)
         self.work_bytes = fdas_normalise_workspace_bytes(self.n)
         self.work = torch.empty(max(self.work_bytes, 16), dtype=torch.uint8, device=dev)
-        self.bank = torch.empty(self.Kb * self.L * 2, dtype=torch.float32, device=dev)
+        self.bank = torch.empty(fdas_bank_floats(self.p), dtype=torch.float32, device=dev)
         self.plane = (torch.empty(self.K * self.row_stride, dtype=torch.float32, device=dev)
                       if plane else None)
         self.cand = torch.empty(self.cap * 4, dtype=torch.int32, device=dev)

@@ -13,10 +13,26 @@ def bank_slot(k, L):
 
 
 def bank_natural(bank_f32, Kb, L):
-    """(Kb, L) complex128 template spectra in natural frequency order."""
-    b = np.asarray(bank_f32, np.float32).reshape(Kb, L, 2)
+    """(Kb, L) complex128 template spectra in natural frequency order, and the
+    (Kb, 16) mirror slots, both restated from the layout in fdas.h."""
+    b = np.asarray(bank_f32, np.float32).reshape(Kb, L + 16, 2)
     c = b[..., 0].astype(np.float64) + 1j * b[..., 1].astype(np.float64)
-    return c[:, bank_slot(np.arange(L), L)]
+    return c[:, bank_slot(np.arange(L), L)], c[:, L:]
+
+
+def mirror_expected(H, L):
+    """Expected mirror slots from natural-order spectra H (Kb, L): complex
+    L + 2j + 1 - e holds H[-k(s)] for slot s = 2(7 - j)T + e (T = L/16), the
+    slot of register 2(7 - j) + e of thread 0."""
+    T = L // 16
+    slot_k = np.empty(L, np.int64)
+    slot_k[bank_slot(np.arange(L), L)] = np.arange(L)
+    out = np.empty((H.shape[0], 16), H.dtype)
+    for j in range(8):
+        for e in range(2):
+            s = 2 * (7 - j) * T + e
+            out[:, 2 * j + 1 - e] = H[:, (-slot_k[s]) % L]
+    return out
 
 
 def sorted_cands(rows, cols, pw):

@@ -33,6 +33,7 @@ def test_host_helpers():
     p = F.params(2048, 256, -200, 200, 2, 1)
     assert F.fdas_num_templates(p) == 201
     assert F.fdas_bank_rows(p) == 101
+    assert F.fdas_bank_floats(p) == 101 * (2048 + 16) * 2
     assert F.fdas_num_segments(p, 1 << 22) == -(-(1 << 22) // 1792)
     assert F.fdas_plane_width(p, 1 << 22) == 1 << 23
     assert F.fdas_plane_width(F.params(2048, 256, -200, 200, 2, 0), 1000) == 1000

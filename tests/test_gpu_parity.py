@@ -13,7 +13,7 @@ import pytest
 
 import oracle.fdas_oracle as O
 import synth
-from tests.gpu_common import bank_natural, compare_candidates
+from tests.gpu_common import bank_natural, compare_candidates, mirror_expected
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,10 +47,11 @@ def _upload_spec(S, A):
 def test_template_bank_matches_oracle(F, L, M, zmin, zmax, zstep):
     p = F.params(L, M, zmin, zmax, zstep, 1)
     Kb = F.fdas_bank_rows(p)
-    bank = torch.empty(Kb * L * 2, dtype=torch.float32, device="cuda")
+    bank = torch.empty(F.fdas_bank_floats(p), dtype=torch.float32, device="cuda")
     F.fdas_make_templates(p, bank)
     torch.cuda.synchronize()
-    H = bank_natural(bank.cpu().numpy(), Kb, L)
+    H, mirror = bank_natural(bank.cpu().numpy(), Kb, L)
+    assert np.array_equal(mirror, mirror_expected(H, L))
     zs = O.z_grid(zmin, zmax, zstep)
     zb = zs[zs >= 0] if zmin == -zmax and zmax > 0 else zs
     assert len(zb) == Kb
