@@ -167,6 +167,33 @@ size_t fdas_normalise_workspace_bytes(int64_t n);
 int fdas_normalise(const float *series, int64_t n, int32_t median_block, float *spec,
                    void *work, size_t work_bytes, void *stream);
 
+/* Largest series length fdas_normalise_noalloc accepts (2^20 samples). */
+#define FDAS_NOALLOC_MAX_N (1 << 20)
+
+/*
+ * fdas_normalise_noalloc -- fdas_normalise without a caller workspace.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they call in, e.g. a real-time pipeline
+ * that reserves all of its device memory at start-up and must not allocate
+ * afterwards (cudaMalloc may synchronise the device, and can fail once memory
+ * is fragmented), or code running inside another program's hook with no
+ * access to an allocator.  The workspace is a fixed device array inside the
+ * library (FDAS_NOALLOC_MAX_N * 4 bytes = 4 MiB per GPU, held by every GPU
+ * that loads the library until the process exits); nothing is allocated or
+ * freed by the call.
+ * The first call on a device looks up that device's copy of the array
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls on a device share the one array: calls that may
+ * overlap on the GPU (different streams, no ordering between them) race and
+ * must not be issued.  The array needs no clearing between calls (every
+ * value is written before it is read).
+ * Arguments, layout and results are those of fdas_normalise.
+ * Errors: FDAS_E_UNSUPPORTED if n > FDAS_NOALLOC_MAX_N; otherwise as
+ * fdas_normalise; FDAS_E_CUDA if the array's address cannot be obtained.
+ */
+int fdas_normalise_noalloc(const float *series, int64_t n, int32_t median_block, float *spec,
+                           void *stream);
+
 /*
  * fdas_correlate -- the fused overlap-save convolver (a4-a7: Section 3
  * Fig. 1 and the text after it; Section 4.1 Fig. 3; Section 4.2 fused

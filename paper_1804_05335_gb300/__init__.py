@@ -15,7 +15,8 @@ __all__ = [
     "FdasError", "fdas_params", "fdas_cand", "fdas_fused_threshold", "load_library", "lib_path",
     "params", "fdas_strerror", "fdas_version", "fdas_half_width", "fdas_num_templates",
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
-    "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_correlate", "fdas_threshold",
+    "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
+    "fdas_correlate", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
     "FDAS_OK", "FDAS_E_INVAL", "FDAS_E_CUDA", "FDAS_E_OVERFLOW", "FDAS_E_TIMEOUT",
     "FDAS_E_UNSUPPORTED",
@@ -34,6 +35,7 @@ FDAS_E_UNSUPPORTED = -5
 FDAS_STATUS_TIMEOUT = 1
 FDAS_STATUS_OVERFLOW = 2
 FDAS_CAND_PEAK = 1
+FDAS_NOALLOC_MAX_N = 1 << 20
 
 c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
@@ -85,6 +87,7 @@ def load_library():
         "fdas_make_templates": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
         "fdas_normalise_workspace_bytes": (c_sz, [c_i64]),
         "fdas_normalise": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]),
+        "fdas_normalise_noalloc": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp]),
         "fdas_correlate": (ctypes.c_int, [P(fdas_params), c_vp, c_i64, c_vp, c_vp, c_i64,
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
@@ -187,6 +190,18 @@ def fdas_normalise(series, n: int, median_block: int, spec, work, work_bytes: in
     _check(load_library().fdas_normalise(_ptr(series), int(n), int(median_block), _ptr(spec),
                                          _ptr(work), int(work_bytes), _stream(stream)),
            "fdas_normalise")
+
+
+def fdas_normalise_noalloc(series, n: int, median_block: int, spec, stream=None) -> None:
+    """fdas_normalise with the library's fixed device workspace (n <= 2^20).
+
+    For callers that must not allocate device memory at call time; see the
+    declaration in include/fdas.h for the limits (one shared workspace per
+    GPU: calls that can overlap on the GPU race).
+    """
+    _check(load_library().fdas_normalise_noalloc(_ptr(series), int(n), int(median_block),
+                                                 _ptr(spec), _stream(stream)),
+           "fdas_normalise_noalloc")
 
 
 def fdas_correlate(p: fdas_params, spec, nb: int, bank, plane, row_stride: int,

@@ -18,6 +18,8 @@
 // the float bit patterns) and scales the block by sqrt(ln 2 / median).
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace fdas {
@@ -281,3 +283,47 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fdas_normalise_noalloc: fdas_normalise with the workspace taken from a
+// fixed device array of this file instead of the caller (for callers that
+// must not allocate device memory when they call in).
+// ---------------------------------------------------------------------------
+namespace fdas {
+
+constexpr size_t kNoallocScratchBytes = (size_t)(FDAS_NOALLOC_MAX_N / 2) * sizeof(float2);
+static __device__ __align__(256) float2 g_noalloc_scratch[FDAS_NOALLOC_MAX_N / 2];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Device address of this device's copy of the array (looked up once per
+// device, with that device current).  In host code the array's name is only
+// a host-side handle, never a device address.
+static int noalloc_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return FDAS_E_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FDAS_E_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FDAS_OK;
+}
+
+}  // namespace fdas
+
+extern "C" int fdas_normalise_noalloc(const float* series, int64_t n, int32_t median_block,
+                                      float* spec, void* stream) {
+    if (n > FDAS_NOALLOC_MAX_N) return FDAS_E_UNSUPPORTED;
+    const size_t need = fdas_normalise_workspace_bytes(n);
+    if (need == 0 || need > fdas::kNoallocScratchBytes) return FDAS_E_INVAL;
+    void* work = nullptr;
+    const int rc = fdas::noalloc_scratch(&work);
+    if (rc != FDAS_OK) return rc;
+    return fdas_normalise(series, n, median_block, spec, work, fdas::kNoallocScratchBytes, stream);
+}
