@@ -234,6 +234,41 @@ int fdas_threshold(const float *plane, int32_t rows, int64_t width, int64_t row_
                    float thr, int32_t want_flags, fdas_cand *out, int32_t cap,
                    int32_t *count, int32_t *status, void *stream);
 
+/*
+ * Candidate refinement over continuous (r, z) (a11).  The paper improves the
+ * (r, z) of a detection by fine-binning the f-fdot plane around it (Section
+ * 5.2, last paragraph); here the correlation power of Eq. 23 is evaluated
+ * off the grid and maximised by gradient ascent:
+ *   S(r, z) = sum_{k=[r]-m}^{[r]+m} spec[k] conj(R_z(k - r)),  P = |S|^2,
+ *   [r] = floor(r + 1/2), spec[k] = 0 outside [0, nb),
+ * with R_z(d) the FP64 template response of fdas_make_templates at real
+ * offset d and real z.  m is the fixed tap half-window (h(zmax) covers every
+ * template of a search).  All arithmetic is FP64 except the spectrum itself.
+ *
+ * fdas_refine_fwd: P[c], dP/dr (dPdr, optional), dP/dz (dPdz, optional) and
+ *   S (re, im pairs, optional) for candidates c < ncand at (r[c], z[c]).
+ * fdas_refine_bwd: accumulates into grad_spec (complex, nb values) the
+ *   gradient of sum_c gP[c] P[c] with respect to the spectrum,
+ *   grad_spec[k] += gP[c] * 2 S[c] R_z(k - r) (derivative with respect to the
+ *   real part plus i times that with respect to the imaginary part); S as
+ *   returned by fdas_refine_fwd.  Uses float atomics: the summation order of
+ *   overlapping candidates is not fixed.
+ * fdas_refine: `steps` steps of gradient ascent on log P per candidate,
+ *   r += clamp(lr_r (dP/dr)/P, -0.5, 0.5), z += clamp(lr_z (dP/dz)/P, -2, 2),
+ *   then r_out, z_out and the final P_out.
+ * Pointers are device pointers; r, z, P, S, gP, r_out, z_out, P_out are
+ * double arrays of ncand (S: 2*ncand).  Errors: FDAS_E_INVAL.
+ */
+int fdas_refine_fwd(const float *spec, int64_t nb, const double *r, const double *z,
+                    int32_t ncand, int32_t m, double *P, double *dPdr, double *dPdz, double *S,
+                    void *stream);
+int fdas_refine_bwd(const float *spec, int64_t nb, const double *r, const double *z,
+                    int32_t ncand, int32_t m, const double *S, const double *gP, float *grad_spec,
+                    void *stream);
+int fdas_refine(const float *spec, int64_t nb, const double *r_in, const double *z_in,
+                int32_t ncand, int32_t m, int32_t steps, double lr_r, double lr_z, double *r_out,
+                double *z_out, double *P_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,9 @@ It computes, slowly and by definition, what the GPU path computes fast:
 * ``power_plane``        full-bin power and interbinned half-bin power
   (Eq. "f-interp", Section 3).
 * ``threshold``          candidates P > T, with the local-maximum flag.
+* ``refine_power``       the correlation power at continuous (r, z) and its
+  derivatives, from the defining integrals by quadrature (Section 5.2's
+  fine-binning around a detection, done as a continuous maximisation).
 
 Readings of the paper that this file relies on (each also listed in the
 design notes):
@@ -54,7 +57,8 @@ __all__ = [
     "half_width", "z_grid", "template_response", "template_taps", "kernel_spectrum",
     "real_spectrum", "normalise", "block_medians", "correlate", "correlate_points",
     "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
-    "search", "oracle_threads", "PEAK_FLAG",
+    "search", "oracle_threads", "PEAK_FLAG", "response_derivs_quadrature", "refine_taps",
+    "refine_power", "refine_grad_spec", "refine_ascent",
 ]
 
 PEAK_FLAG = 1
@@ -385,3 +389,72 @@ def search(x, zmin, zmax, zstep, block=1024, thr=20.0, interbin=True):
     zs = z_grid(zmin, zmax, zstep)
     P = plane(A, zs, interbin)
     return A, P, threshold(P, thr)
+
+
+# --------------------------------------------------------------------------
+# candidate refinement over continuous (r, z)
+# --------------------------------------------------------------------------
+def response_derivs_quadrature(z: float, d):
+    """R_z(d), dR/dd, dR/dz by composite 16-point Gauss-Legendre quadrature of
+    their defining integrals (vectorised over d):
+        R     = int_0^1 e^{i phi} du,
+        dR/dd = int_0^1 (-i 2 pi u) e^{i phi} du,
+        dR/dz = int_0^1 i pi (u^2 - u) e^{i phi} du,
+    phi(u) = 2 pi (z u^2/2 - (d + z/2) u).  Panels hold at most one cycle."""
+    d = np.atleast_1d(np.asarray(d, np.float64))
+    x, w = np.polynomial.legendre.leggauss(16)
+    panels = int(math.ceil(np.max(np.abs(d)) + abs(z) + 2.0))
+    edges = np.linspace(0.0, 1.0, panels + 1)
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    half = 0.5 * (edges[1:] - edges[:-1])
+    u = (mid[:, None] + half[:, None] * x[None, :]).ravel()
+    ww = (half[:, None] * w[None, :]).ravel()
+    ph = 2.0 * np.pi * (z * u[None, :] ** 2 / 2.0 - (d[:, None] + z / 2.0) * u[None, :])
+    e = ww[None, :] * np.exp(1j * ph)
+    R = e.sum(1)
+    Rd = (e * (-2j * np.pi * u[None, :])).sum(1)
+    Rz = (e * (1j * np.pi * (u[None, :] ** 2 - u[None, :]))).sum(1)
+    return R, Rd, Rz
+
+
+def refine_taps(nb: int, r: float, m: int):
+    """Tap bins k = [r]-m .. [r]+m inside [0, nb) and offsets d = k - r."""
+    k0 = int(math.floor(r + 0.5))
+    k = np.arange(k0 - m, k0 + m + 1)
+    k = k[(k >= 0) & (k < nb)]
+    return k, k - float(r)
+
+
+def refine_power(A, r: float, z: float, m: int):
+    """P = |S|^2 with S = sum_k A_k conj(R_z(k - r)), and dP/dr, dP/dz, S."""
+    A = np.asarray(A)
+    k, d = refine_taps(A.shape[0], r, m)
+    R, Rd, Rz = response_derivs_quadrature(z, d)
+    a = A[k].astype(np.complex128)
+    S = np.sum(a * np.conj(R))
+    Sr = np.sum(a * np.conj(-Rd))
+    Sz = np.sum(a * np.conj(Rz))
+    P = abs(S) ** 2
+    return P, 2.0 * np.real(np.conj(S) * Sr), 2.0 * np.real(np.conj(S) * Sz), S
+
+
+def refine_grad_spec(A, r: float, z: float, m: int):
+    """dP/dA_k (d/dRe + i d/dIm) = 2 S R_z(k - r) at the taps k."""
+    k, d = refine_taps(np.asarray(A).shape[0], r, m)
+    R, _, _ = response_derivs_quadrature(z, d)
+    _, _, _, S = refine_power(A, r, z, m)
+    return k, 2.0 * S * R
+
+
+def refine_ascent(A, r0: float, z0: float, m: int, steps: int = 20, lr_r: float = 0.15,
+                  lr_z: float = 9.0):
+    """Gradient ascent on log P: r += clamp(lr_r P_r/P, +-0.5), z += clamp(lr_z P_z/P, +-2)."""
+    r, z = float(r0), float(z0)
+    P = 0.0
+    for it in range(steps + 1):
+        P, gr, gz, _ = refine_power(A, r, z, m)
+        if it == steps or not P > 0.0:
+            break
+        r += min(max(lr_r * gr / P, -0.5), 0.5)
+        z += min(max(lr_z * gz / P, -2.0), 2.0)
+    return r, z, P

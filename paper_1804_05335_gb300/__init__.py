@@ -17,6 +17,7 @@ __all__ = [
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
+    "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
     "FDAS_OK", "FDAS_E_INVAL", "FDAS_E_CUDA", "FDAS_E_OVERFLOW", "FDAS_E_TIMEOUT",
     "FDAS_E_UNSUPPORTED",
@@ -92,6 +93,12 @@ def load_library():
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
+        "fdas_refine_fwd": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
+                                           c_vp, c_vp, c_vp]),
+        "fdas_refine_bwd": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
+                                           c_vp, c_vp]),
+        "fdas_refine": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i32, c_i32, c_i32,
+                                       ctypes.c_double, ctypes.c_double, c_vp, c_vp, c_vp, c_vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -218,3 +225,24 @@ def fdas_threshold(plane, rows: int, width: int, row_stride: int, thr: float, wa
                                          float(thr), int(want_flags), _ptr(out), int(cap),
                                          _ptr(count), _ptr(status), _stream(stream)),
            "fdas_threshold")
+
+
+def fdas_refine_fwd(spec, nb: int, r, z, ncand: int, m: int, P, dPdr=None, dPdz=None, S=None,
+                    stream=None) -> None:
+    _check(load_library().fdas_refine_fwd(_ptr(spec), int(nb), _ptr(r), _ptr(z), int(ncand),
+                                          int(m), _ptr(P), _ptr(dPdr), _ptr(dPdz), _ptr(S),
+                                          _stream(stream)), "fdas_refine_fwd")
+
+
+def fdas_refine_bwd(spec, nb: int, r, z, ncand: int, m: int, S, gP, grad_spec,
+                    stream=None) -> None:
+    _check(load_library().fdas_refine_bwd(_ptr(spec), int(nb), _ptr(r), _ptr(z), int(ncand),
+                                          int(m), _ptr(S), _ptr(gP), _ptr(grad_spec),
+                                          _stream(stream)), "fdas_refine_bwd")
+
+
+def fdas_refine(spec, nb: int, r_in, z_in, ncand: int, m: int, steps: int, lr_r: float,
+                lr_z: float, r_out, z_out, P_out, stream=None) -> None:
+    _check(load_library().fdas_refine(_ptr(spec), int(nb), _ptr(r_in), _ptr(z_in), int(ncand),
+                                      int(m), int(steps), float(lr_r), float(lr_z), _ptr(r_out),
+                                      _ptr(z_out), _ptr(P_out), _stream(stream)), "fdas_refine")

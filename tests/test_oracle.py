@@ -264,3 +264,59 @@ def test_injection_recovered_off_grid_within_paper_tolerance():
         k, c = np.unravel_index(np.argmax(sub), sub.shape)
         assert abs((lo + c) / 2.0 - r0) <= 0.5 + 1e-9
         assert abs(zs[k] - z0) <= wl.zstep
+
+
+# ---------------------------------------------------------------- refinement
+def test_response_derivatives_match_finite_differences():
+    for z in (150.0, 7.3, 0.3, 0.0, -42.0):
+        d = np.array([-60.2, -3.5, 0.0, 0.45, 12.0])
+        R, Rd, Rz = O.response_derivs_quadrature(z, d)
+        assert np.abs(R - O.template_response(z, d)).max() < 1e-11
+        h = 1e-5
+        Rdp = O.response_derivs_quadrature(z, d + h)[0]
+        Rdm = O.response_derivs_quadrature(z, d - h)[0]
+        Rzp = O.response_derivs_quadrature(z + h, d)[0]
+        Rzm = O.response_derivs_quadrature(z - h, d)[0]
+        assert np.abs((Rdp - Rdm) / (2 * h) - Rd).max() < 1e-6
+        assert np.abs((Rzp - Rzm) / (2 * h) - Rz).max() < 1e-6
+
+
+def test_refine_power_on_grid_equals_tap_sum():
+    # at an integer bin and a grid z, with m = h(z), P is |F_z(r)|^2 of Eq. 23
+    A = synth.random_spectrum(600, 8).astype(np.complex128)
+    for z in (-14.0, 0.0, 6.0):
+        m = O.half_width(z)
+        F = O.correlate(A, [z], 250, 1)[0, 0]
+        P, _, _, S = O.refine_power(A, 250.0, z, m)
+        assert abs(S - F) < 1e-10 and abs(P - abs(F) ** 2) < 1e-9
+
+
+def test_refine_gradients_match_finite_differences():
+    A = synth.random_spectrum(400, 9).astype(np.complex128)
+    m = 20
+    for r, z in ((150.3, 4.2), (201.49, -7.9), (90.0, 0.25)):
+        P, gr, gz, _ = O.refine_power(A, r, z, m)
+        h = 1e-5
+        fr = (O.refine_power(A, r + h, z, m)[0] - O.refine_power(A, r - h, z, m)[0]) / (2 * h)
+        fz = (O.refine_power(A, r, z + h, m)[0] - O.refine_power(A, r, z - h, m)[0]) / (2 * h)
+        assert abs(fr - gr) < 1e-5 * (1 + abs(gr)) and abs(fz - gz) < 1e-5 * (1 + abs(gz))
+        k, g = O.refine_grad_spec(A, r, z, m)
+        for idx in (0, len(k) // 2, len(k) - 1):
+            Ap, Am = A.copy(), A.copy()
+            Ap[k[idx]] += h
+            Am[k[idx]] -= h
+            dre = (O.refine_power(Ap, r, z, m)[0] - O.refine_power(Am, r, z, m)[0]) / (2 * h)
+            Ap, Am = A.copy(), A.copy()
+            Ap[k[idx]] += 1j * h
+            Am[k[idx]] -= 1j * h
+            dim = (O.refine_power(Ap, r, z, m)[0] - O.refine_power(Am, r, z, m)[0]) / (2 * h)
+            assert abs((dre + 1j * dim) - g[idx]) < 1e-6 * (1 + abs(g[idx]))
+
+
+def test_refine_ascent_finds_an_injected_chirp():
+    n, r0, z0 = 1 << 14, 3000.37, 7.4
+    x = synth.make_series(n, ((r0, z0, 40.0),), seed=31)
+    A = O.normalise(O.real_spectrum(x), 1024)
+    r, z, P = O.refine_ascent(A, 3000.5, 8.0, m=O.half_width(20), steps=20)
+    assert abs(r - r0) < 0.05 and abs(z - z0) < 0.3
+    assert P > O.refine_power(A, 3000.5, 8.0, O.half_width(20))[0]
