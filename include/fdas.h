@@ -218,6 +218,47 @@ int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const fl
                    int32_t *status, void *stream);
 
 /*
+ * Batched search over many series (a10), e.g. the dispersion trials of one
+ * observation, each with its own length: one persistent launch walks the
+ * (trial, segment, template) work items of all trials with the same static
+ * balancing as fdas_correlate, so uneven lengths share the GPU evenly.
+ */
+typedef struct {
+    const float *spec;      /* (device) nb complex, 8-byte aligned */
+    int64_t nb;             /* bins of this series (>= 1) */
+    float *plane;           /* (device) K rows of row_stride floats, 16-byte aligned */
+    int64_t row_stride;     /* >= fdas_plane_width(p, nb), multiple of 4 */
+    int64_t item_begin;     /* first work item of this trial (set by fdas_batch_plan) */
+} fdas_trial;
+
+/* Launch tuning (NULL or 0 fields = defaults). */
+typedef struct {
+    int32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = the occupancy maximum */
+} fdas_tuning;
+
+/*
+ * fdas_batch_plan -- validate a host array of trials for p and fill each
+ * item_begin; returns the total number of work items (< 0: FDAS_E_INVAL).
+ * Copy the array unchanged to device memory for fdas_correlate_batched.
+ */
+int64_t fdas_batch_plan(const fdas_params *p, fdas_trial *trials, int32_t ntrials);
+
+/*
+ * fdas_correlate_batched -- fdas_correlate for ntrials series in one launch.
+ * trials: (device) the array planned by fdas_batch_plan; total_items its
+ * return value.  Every plane gets what fdas_correlate would write for its
+ * series.  With `fused`, candidates of all trials go to one list, the
+ * trial's position in `trials` in bits 8..31 of fdas_cand.flags.  The call
+ * only launches kernels (and resets the fused count), so it can be captured
+ * into a CUDA graph once it has run once on the device.  Errors: FDAS_E_INVAL for bad params,
+ * pointers or counts (the device array itself is not re-validated).
+ */
+int fdas_correlate_batched(const fdas_params *p, const fdas_trial *trials, int32_t ntrials,
+                           int64_t total_items, const float *bank,
+                           const fdas_fused_threshold *fused, const fdas_tuning *tuning,
+                           int32_t *status, void *stream);
+
+/*
  * fdas_threshold -- candidates of a power plane (a8: Section 3, comparing
  * the Fourier power with a pre-computed threshold).
  * Emits every (row, col) with plane value > thr (strict).  With

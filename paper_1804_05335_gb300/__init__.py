@@ -17,7 +17,8 @@ __all__ = [
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
-    "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine",
+    "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
+    "fdas_batch_plan", "fdas_correlate_batched",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
     "FDAS_OK", "FDAS_E_INVAL", "FDAS_E_CUDA", "FDAS_E_OVERFLOW", "FDAS_E_TIMEOUT",
     "FDAS_E_UNSUPPORTED",
@@ -52,6 +53,15 @@ class fdas_cand(ctypes.Structure):
 
 class fdas_fused_threshold(ctypes.Structure):
     _fields_ = [("thr", c_f32), ("out", c_vp), ("cap", c_i32), ("count", c_vp)]
+
+
+class fdas_trial(ctypes.Structure):
+    _fields_ = [("spec", c_vp), ("nb", c_i64), ("plane", c_vp), ("row_stride", c_i64),
+                ("item_begin", c_i64)]
+
+
+class fdas_tuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", c_i32)]
 
 
 class FdasError(RuntimeError):
@@ -93,6 +103,10 @@ def load_library():
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
+        "fdas_batch_plan": (c_i64, [P(fdas_params), P(fdas_trial), c_i32]),
+        "fdas_correlate_batched": (ctypes.c_int, [P(fdas_params), c_vp, c_i32, c_i64, c_vp,
+                                                  P(fdas_fused_threshold), P(fdas_tuning), c_vp,
+                                                  c_vp]),
         "fdas_refine_fwd": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
                                            c_vp, c_vp, c_vp]),
         "fdas_refine_bwd": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp,
@@ -246,3 +260,20 @@ def fdas_refine(spec, nb: int, r_in, z_in, ncand: int, m: int, steps: int, lr_r:
     _check(load_library().fdas_refine(_ptr(spec), int(nb), _ptr(r_in), _ptr(z_in), int(ncand),
                                       int(m), int(steps), float(lr_r), float(lr_z), _ptr(r_out),
                                       _ptr(z_out), _ptr(P_out), _stream(stream)), "fdas_refine")
+
+
+def fdas_batch_plan(p: fdas_params, trials) -> int:
+    """trials: ctypes array of fdas_trial (host); fills item_begin, returns total items."""
+    return _check(load_library().fdas_batch_plan(ctypes.byref(p), trials, len(trials)),
+                  "fdas_batch_plan")
+
+
+def fdas_correlate_batched(p: fdas_params, trials_dev, ntrials: int, total_items: int, bank,
+                           fused: fdas_fused_threshold | None = None, ctas_per_sm: int = 0,
+                           status=None, stream=None) -> None:
+    f = ctypes.byref(fused) if fused is not None else None
+    tun = fdas_tuning(int(ctas_per_sm))
+    _check(load_library().fdas_correlate_batched(ctypes.byref(p), _ptr(trials_dev), int(ntrials),
+                                                 int(total_items), _ptr(bank), f,
+                                                 ctypes.byref(tun), _ptr(status),
+                                                 _stream(stream)), "fdas_correlate_batched")

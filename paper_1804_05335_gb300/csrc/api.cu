@@ -119,4 +119,44 @@ int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const fl
                             status, (cudaStream_t)stream);
 }
 
+int64_t fdas_batch_plan(const fdas_params* p, fdas_trial* trials, int32_t ntrials) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    if (!trials || ntrials < 1) return FDAS_E_INVAL;
+    const int64_t B = p->L - p->M;
+    int64_t items = 0;
+    for (int32_t i = 0; i < ntrials; ++i) {
+        fdas_trial& t = trials[i];
+        if (!t.spec || !t.plane || t.nb < 1 || t.nb > ((int64_t)1 << 31)) return FDAS_E_INVAL;
+        if (!aligned(t.spec, 8) || !aligned(t.plane, 16)) return FDAS_E_INVAL;
+        const int64_t width = p->interbin ? 2 * t.nb : t.nb;
+        if (t.row_stride < width || (t.row_stride % 4) != 0) return FDAS_E_INVAL;
+        t.item_begin = items;
+        items += ((t.nb + B - 1) / B) * g.K;
+    }
+    return items;
+}
+
+int fdas_correlate_batched(const fdas_params* p, const fdas_trial* trials, int32_t ntrials,
+                           int64_t total_items, const float* bank,
+                           const fdas_fused_threshold* fused, const fdas_tuning* tuning,
+                           int32_t* status, void* stream) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    if (!trials || ntrials < 1 || ntrials > (1 << 23) || total_items < 1 || !bank) return FDAS_E_INVAL;
+    if (!aligned(trials, 8) || !aligned(bank, 16)) return FDAS_E_INVAL;
+    if (fused) {
+        if (!fused->out || !fused->count || fused->cap < 0) return FDAS_E_INVAL;
+        if (!aligned(fused->out, 4) || !aligned(fused->count, 4)) return FDAS_E_INVAL;
+    }
+    if (status && !aligned(status, 4)) return FDAS_E_INVAL;
+    const int cps = tuning ? tuning->ctas_per_sm : 0;
+    if (cps < 0) return FDAS_E_INVAL;
+    return launch_correlate_batched(p, g, trials, ntrials, total_items,
+                                    reinterpret_cast<const float4*>(bank), fused, cps, status,
+                                    (cudaStream_t)stream);
+}
+
 }  // extern "C"

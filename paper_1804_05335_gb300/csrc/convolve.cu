@@ -53,6 +53,8 @@ struct ConvArgs {
     int32_t cap;
     int32_t* count;
     int32_t* status;
+    const fdas_trial* trials;   // batched launches: device table of ntrials series
+    int32_t ntrials;
 };
 
 template <int L>
@@ -66,14 +68,14 @@ struct ConvSmem {
 // polls of the template-row bulk copy before the kernel gives up
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-__device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, float v) {
+__device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, float v, int flags) {
     int idx = atomicAdd(A.count, 1);
     if (idx < A.cap) {
         fdas_cand c;
         c.z_idx = row;
         c.col = (int32_t)col;
         c.power = v;
-        c.flags = 0;
+        c.flags = flags;
         A.cand[idx] = c;
     } else if (A.status) {
         atomicOr(A.status, FDAS_STATUS_OVERFLOW);
@@ -105,7 +107,40 @@ __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
                        fmaf(x01.z, x01.z, x01.w * x01.w), hs * fmaf(dx1, dx1, dy1 * dy1));
 }
 
-template <int L, bool FUSE>
+// Series state of the item being processed: one series for fdas_correlate,
+// the trial table entry for fdas_correlate_batched.
+struct SeriesState {
+    const float2* spec;
+    int64_t nb;
+    float* plane;
+    int64_t row_stride;
+    int64_t end;   // first item of the next series
+    int flags;     // candidate flags: trial index << 8 in batched launches
+};
+
+template <bool BATCH>
+__device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
+    SeriesState st;
+    if constexpr (BATCH) {
+        const fdas_trial& tr = A.trials[trial];
+        st.spec = reinterpret_cast<const float2*>(tr.spec);
+        st.nb = tr.nb;
+        st.plane = tr.plane;
+        st.row_stride = tr.row_stride;
+        st.end = (trial + 1 < A.ntrials) ? A.trials[trial + 1].item_begin : A.items;
+        st.flags = trial << 8;
+    } else {
+        st.spec = A.spec;
+        st.nb = A.nb;
+        st.plane = A.plane;
+        st.row_stride = A.row_stride;
+        st.end = A.items;
+        st.flags = 0;
+    }
+    return st;
+}
+
+template <int L, bool FUSE, bool BATCH>
 __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const ConvArgs A) {
     using S = ConvShape<L>;
     constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
@@ -124,8 +159,20 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
     const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
     if (lo >= hi) return;
-    int64_t s = lo / A.K;
-    int q = (int)(lo - s * A.K);
+    int trial = 0;
+    if constexpr (BATCH) {
+        // last trial whose first item is <= lo
+        int a0 = 0, a1 = A.ntrials - 1;
+        while (a0 < a1) {
+            const int mid = (a0 + a1 + 1) >> 1;
+            if (A.trials[mid].item_begin <= lo) a0 = mid; else a1 = mid - 1;
+        }
+        trial = a0;
+    }
+    SeriesState st = series_of<BATCH>(A, trial);
+    const int64_t first = BATCH ? A.trials[trial].item_begin : 0;
+    int64_t s = (lo - first) / A.K;
+    int q = (int)(lo - first - s * A.K);
     int row, brow, cj;
     item_row(A, q, row, brow, cj);
 
@@ -165,6 +212,15 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     const float4* hb4 = reinterpret_cast<const float4*>(hbuf);
 
     for (int64_t w = lo; w < hi; ++w) {
+        if constexpr (BATCH) {
+            if (w == st.end) {   // next trial: its first segment and template
+                ++trial;
+                st = series_of<BATCH>(A, trial);
+                s = 0;
+                q = 0;
+                cur_seg = -1;
+            }
+        }
         if (s != cur_seg) {
             // ---- forward FFT of segment s, once per segment ----
             cur_seg = s;
@@ -172,7 +228,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int64_t pos = base + i * T + t;
-                v[i] = (pos >= 0 && pos < A.nb) ? __ldg(&A.spec[pos]) : make_float2(0.f, 0.f);
+                v[i] = (pos >= 0 && pos < st.nb) ? __ldg(&st.spec[pos]) : make_float2(0.f, 0.f);
             }
             forward_fft_d3<L>(v, buf0, buf1, t);
 #pragma unroll
@@ -260,11 +316,11 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 
         // ---- epilogue: powers of positions M/2 .. M/2+B, two bins per pair ----
         const int64_t r0 = s * (int64_t)B;
-        float* prow = A.plane + (int64_t)row * A.row_stride;
+        float* prow = st.plane + (int64_t)row * st.row_stride;
         const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
         const float2* o2 = outb + M / 2 + 2;
         float mx = 0.f;
-        if (r0 + B < A.nb) {
+        if (r0 + B < st.nb) {
             constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
             if (A.interbin) {
                 float4* dst = reinterpret_cast<float4*>(prow + 2 * r0);
@@ -294,18 +350,18 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
             // segment reaching the end of the spectrum: per-bin checks
             for (int p = t; p < NP; p += T) {
                 const int64_t r = r0 + 2 * p;
-                if (r >= A.nb) break;
+                if (r >= st.nb) break;
                 float4 pw = pair_powers(o4[p], o2[2 * p]);
-                if (r + 1 >= A.nb - 1) pw.w = 0.f;       // no bin r+2
-                if (r >= A.nb - 1) pw.y = 0.f;           // no bin r+1
-                if (r + 1 >= A.nb) { pw.z = 0.f; pw.w = 0.f; }
+                if (r + 1 >= st.nb - 1) pw.w = 0.f;       // no bin r+2
+                if (r >= st.nb - 1) pw.y = 0.f;           // no bin r+1
+                if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
                 if (A.interbin) {
                     prow[2 * r] = pw.x;
                     prow[2 * r + 1] = pw.y;
-                    if (r + 1 < A.nb) { prow[2 * r + 2] = pw.z; prow[2 * r + 3] = pw.w; }
+                    if (r + 1 < st.nb) { prow[2 * r + 2] = pw.z; prow[2 * r + 3] = pw.w; }
                 } else {
                     prow[r] = pw.x;
-                    if (r + 1 < A.nb) prow[r + 1] = pw.z;
+                    if (r + 1 < st.nb) prow[r + 1] = pw.z;
                     pw.y = 0.f;
                     pw.w = 0.f;
                 }
@@ -317,19 +373,19 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 // rare: rescan this thread's pairs and emit each crossing
                 for (int p = t; p < NP; p += T) {
                     const int64_t r = r0 + 2 * p;
-                    if (r >= A.nb) break;
+                    if (r >= st.nb) break;
                     float4 pw = pair_powers(o4[p], o2[2 * p]);
-                    if (r + 1 >= A.nb - 1) pw.w = 0.f;
-                    if (r >= A.nb - 1) pw.y = 0.f;
-                    if (r + 1 >= A.nb) { pw.z = 0.f; pw.w = 0.f; }
+                    if (r + 1 >= st.nb - 1) pw.w = 0.f;
+                    if (r >= st.nb - 1) pw.y = 0.f;
+                    if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
                     if (A.interbin) {
-                        if (pw.x > A.thr) emit(A, row, 2 * r, pw.x);
-                        if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y);
-                        if (pw.z > A.thr) emit(A, row, 2 * r + 2, pw.z);
-                        if (pw.w > A.thr) emit(A, row, 2 * r + 3, pw.w);
+                        if (pw.x > A.thr) emit(A, row, 2 * r, pw.x, st.flags);
+                        if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y, st.flags);
+                        if (pw.z > A.thr) emit(A, row, 2 * r + 2, pw.z, st.flags);
+                        if (pw.w > A.thr) emit(A, row, 2 * r + 3, pw.w, st.flags);
                     } else {
-                        if (pw.x > A.thr) emit(A, row, r, pw.x);
-                        if (pw.z > A.thr) emit(A, row, r + 1, pw.z);
+                        if (pw.x > A.thr) emit(A, row, r, pw.x, st.flags);
+                        if (pw.z > A.thr) emit(A, row, r + 1, pw.z, st.flags);
                     }
                 }
             }
@@ -343,42 +399,60 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     }
 }
 
-template <int L, bool FUSE>
-static int launch_one(const ConvArgs& args, cudaStream_t st) {
+template <int L, bool FUSE, bool BATCH>
+static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     using S = ConvShape<L>;
     constexpr size_t smem = ConvSmem<L>::bytes;
-    static int grid = 0;
-    if (grid == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE>,
+    static int sms = 0, max_per_sm = 0;
+    if (sms == 0) {
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return FDAS_E_CUDA;
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, n = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE>, S::T, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH>,
+                                                          S::T, smem) != cudaSuccess)
             return FDAS_E_CUDA;
         if (per_sm < 1) return FDAS_E_UNSUPPORTED;
-        grid = sms * per_sm;
+        max_per_sm = per_sm;
+        sms = n;
     }
-    int64_t g = std::min<int64_t>(grid, std::max<int64_t>(1, args.items));
-    conv_kernel<L, FUSE><<<(unsigned)g, S::T, smem, st>>>(args);
+    const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
+    const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
+    conv_kernel<L, FUSE, BATCH><<<(unsigned)g, S::T, smem, st>>>(args);
     return cuda_status(cudaGetLastError());
 }
 
-int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
-                     const float4* bank, float* plane, int64_t row_stride,
-                     const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st) {
+template <bool BATCH>
+static int dispatch(const fdas_params* p, const ConvArgs& a, bool fused, int ctas_per_sm,
+                    cudaStream_t st) {
+    switch (p->L) {
+        case 1024:
+            return fused ? launch_one<1024, true, BATCH>(a, ctas_per_sm, st)
+                         : launch_one<1024, false, BATCH>(a, ctas_per_sm, st);
+        case 2048:
+            return fused ? launch_one<2048, true, BATCH>(a, ctas_per_sm, st)
+                         : launch_one<2048, false, BATCH>(a, ctas_per_sm, st);
+        case 4096:
+            return fused ? launch_one<4096, true, BATCH>(a, ctas_per_sm, st)
+                         : launch_one<4096, false, BATCH>(a, ctas_per_sm, st);
+        default:
+            return FDAS_E_INVAL;
+    }
+}
+
+static ConvArgs base_args(const fdas_params* p, const Grid& g, const float4* bank,
+                          const fdas_fused_threshold* fused, int32_t* status) {
     ConvArgs a;
-    a.spec = spec;
-    a.nb = nb;
+    a.spec = nullptr;
+    a.nb = 0;
+    a.plane = nullptr;
+    a.row_stride = 0;
+    a.items = 0;
     a.bank = bank;
-    a.plane = plane;
-    a.row_stride = row_stride;
-    const int64_t B = p->L - p->M;
-    const int64_t nseg = (nb + B - 1) / B;
-    a.items = nseg * g.K;
     a.K = g.K;
     a.j0 = g.j0;
     a.sym = g.sym;
@@ -390,17 +464,41 @@ int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, in
     a.cap = fused ? fused->cap : 0;
     a.count = fused ? fused->count : nullptr;
     a.status = status;
+    a.trials = nullptr;
+    a.ntrials = 0;
+    return a;
+}
+
+int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
+                     const float4* bank, float* plane, int64_t row_stride,
+                     const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st) {
+    ConvArgs a = base_args(p, g, bank, fused, status);
+    a.spec = spec;
+    a.nb = nb;
+    a.plane = plane;
+    a.row_stride = row_stride;
+    const int64_t B = p->L - p->M;
+    a.items = ((nb + B - 1) / B) * g.K;
     if (fused) {
         cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return FDAS_E_CUDA;
     }
-    const bool f = fused != nullptr;
-    switch (p->L) {
-        case 1024: return f ? launch_one<1024, true>(a, st) : launch_one<1024, false>(a, st);
-        case 2048: return f ? launch_one<2048, true>(a, st) : launch_one<2048, false>(a, st);
-        case 4096: return f ? launch_one<4096, true>(a, st) : launch_one<4096, false>(a, st);
-        default: return FDAS_E_INVAL;
+    return dispatch<false>(p, a, fused != nullptr, 0, st);
+}
+
+int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_trial* trials,
+                             int32_t ntrials, int64_t total_items, const float4* bank,
+                             const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
+                             cudaStream_t st) {
+    ConvArgs a = base_args(p, g, bank, fused, status);
+    a.trials = trials;
+    a.ntrials = ntrials;
+    a.items = total_items;
+    if (fused) {
+        cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return FDAS_E_CUDA;
     }
+    return dispatch<true>(p, a, fused != nullptr, ctas_per_sm, st);
 }
 
 }  // namespace fdas

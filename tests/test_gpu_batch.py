@@ -1,0 +1,101 @@
+"""Batched persistent launch (a10): every trial's plane and candidates equal
+what the single-series call gives (same kernel arithmetic, bit-exact), a
+captured CUDA graph replays the whole batch, the autotuner picks a valid
+configuration, and one trial is checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle.fdas_oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_05335_gb300 as F
+    F.load_library()
+    return F
+
+
+def _batch(F, ns, L=1024, M=64, pool=1 << 30, cps=0, thr=8.0):
+    from paper_1804_05335_gb300.batch import BatchSearch
+    return BatchSearch(ns, L, M, -20, 20, 2, thr=thr, pool_bytes=pool, ctas_per_sm=cps)
+
+
+def test_batched_equals_single_series(F):
+    from paper_1804_05335_gb300.search import Search
+    ns = [1 << 14, 1 << 13, 1 << 16, 1 << 13, 1 << 15]
+    bs = _batch(F, ns, pool=6 << 20)          # small pool: several waves
+    assert len(bs.waves) > 1
+    xs = [synth.make_series(n, ((n / 5 + 0.3, 6.0, 20.0),), 100 + i) for i, n in enumerate(ns)]
+    for i, x in enumerate(xs):
+        bs.set_series(i, x)
+    bs.front(stream=None)
+    planes = {}
+    for k, w in enumerate(bs.waves):
+        bs.correlate_wave(k)
+        torch.cuda.synchronize()
+        for i in w:
+            planes[i] = bs.plane_of(i).cpu().numpy().copy()
+    cands, counts = bs.candidates()
+    for i, n in enumerate(ns):
+        S = Search(n, 1024, 64, -20, 20, 2, thr=8.0)
+        S.series.copy_(torch.from_numpy(xs[i]))
+        S.step()
+        torch.cuda.synchronize()
+        assert np.array_equal(S.spec.cpu().numpy(), bs.spec_of(i).cpu().numpy())
+        assert np.array_equal(S.plane2d().cpu().numpy(), planes[i])
+        r, c, p, fl, total = S.candidates()
+        br, bc, bp = cands[i]
+        assert np.array_equal(r, br) and np.array_equal(c, bc) and np.array_equal(p, bp)
+
+
+def test_batched_trial_against_oracle(F):
+    ns = [1 << 13, 1 << 14]
+    bs = _batch(F, ns)
+    xs = [synth.make_series(n, ((n / 3, -8.0, 18.0),), 200 + i) for i, n in enumerate(ns)]
+    for i, x in enumerate(xs):
+        bs.set_series(i, x)
+    bs.run()
+    torch.cuda.synchronize()
+    A = O.normalise(O.real_spectrum(xs[1]), 1024)
+    ref = O.plane(A, O.z_grid(-20, 20, 2))
+    assert np.abs(bs.plane_of(1).cpu().numpy() - ref).max() < 1e-3
+
+
+def test_batched_graph_replay(F):
+    ns = [1 << 14, 1 << 13, 1 << 15]
+    bs = _batch(F, ns, pool=1 << 30)
+    for i, n in enumerate(ns):
+        bs.set_series(i, synth.make_series(n, ((n / 7, 4.0, 25.0),), 300 + i))
+    bs.capture()
+    torch.cuda.synchronize()
+    ref_planes = [bs.plane_of(i).cpu().numpy().copy() for i in range(len(ns))]
+    ref_c, ref_n = bs.candidates()
+    bs.pool.fill_(-1.0)
+    bs.count.fill_(-5)
+    bs.replay()
+    torch.cuda.synchronize()
+    for i in range(len(ns)):
+        assert np.array_equal(bs.plane_of(i).cpu().numpy(), ref_planes[i])
+    c, n = bs.candidates()
+    assert np.array_equal(n, ref_n)
+    for i in range(len(ns)):
+        for a, b in zip(c[i], ref_c[i]):
+            assert np.array_equal(a, b)
+
+
+def test_autotune_picks_a_candidate(F, tmp_path):
+    from paper_1804_05335_gb300.autotune import autotune
+    path = str(tmp_path / "tune.json")
+    res = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=((1024, 0), (2048, 0), (2048, 1)),
+                   cache_path=path)
+    assert (res["L"], res["ctas_per_sm"]) in ((1024, 0), (2048, 0), (2048, 1))
+    assert len(res["ms"]) == 3 and all(v > 0 for v in res["ms"].values())
+    again = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=((1024, 0), (2048, 0), (2048, 1)),
+                     cache_path=path)
+    assert again == res
