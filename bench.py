@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--cap", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the batched / refinement / split-precision measurements")
+    ap.add_argument("--batch-trials", type=int, default=256)
     return ap.parse_args()
 
 
@@ -219,6 +222,99 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- scope rows
+def batched_row(args, torch, dev):
+    """256 dispersion trials of uneven length (2^20..2^23 samples, log-uniform
+    over the FFT sizes), 0-2 injections each; autotuned, graph-captured."""
+    from paper_1804_05335_gb300.autotune import autotune
+    from paper_1804_05335_gb300.batch import BatchSearch
+    rng = np.random.default_rng(3)
+    ntr = args.batch_trials
+    ns = [1 << int(p) for p in rng.integers(20, 24, ntr)]
+    probe = ns[:8]
+    t0 = time.perf_counter()
+    tune = autotune(probe, 256, -200, 200, 2, use_cache=False)
+    t_tune = time.perf_counter() - t0
+    bs = BatchSearch(ns, tune["L"], 256, -200, 200, 2, thr=20.0, ctas_per_sm=tune["ctas_per_sm"],
+                     pool_bytes=48 << 30, cap_per_wave=1 << 16, device=dev)
+    host = []
+    for i, n in enumerate(ns):
+        k = int(rng.integers(0, 3))
+        inj = tuple((float(rng.uniform(1e4, 0.45 * n)), float(rng.uniform(-200, 200)),
+                     float(rng.uniform(8, 20))) for _ in range(k))
+        x = synth.make_series(n, inj, 1000 + i)
+        bs.set_series(i, torch.from_numpy(x))
+    bs.capture()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        bs.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    cands, counts = bs.candidates()
+    return {"trials": ntr, "sizes": {str(k): int(v) for k, v in zip(*np.unique(ns, return_counts=True))},
+            "waves": len(bs.waves), "plane_points": bs.plane_points,
+            "ms_per_batch": ms, "points_per_s": bs.plane_points / (ms / 1e3),
+            "candidates": int(sum(len(v[0]) for v in cands.values())),
+            "autotune": tune, "autotune_s": t_tune,
+            "launch": "one CUDA graph: bank + %d front ends + %d persistent convolver launches"
+                      % (ntr, len(bs.waves))}
+
+
+def refine_row(args, torch, dev, S, wl):
+    """Top 10^4 plane points of the production series plus 64 injected truths,
+    20 steps of gradient ascent each."""
+    from paper_1804_05335_gb300 import fdas_half_width
+    from paper_1804_05335_gb300.refine import refine
+    # the 10^4 strongest plane points (all points above 12 are listed first)
+    from paper_1804_05335_gb300 import fdas_threshold
+    cap = 1 << 18
+    out = torch.empty(4 * cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    fdas_threshold(S.plane, S.K, S.width, S.row_stride, 12.0, 0, out, cap, cnt, None)
+    k = min(int(cnt.item()), cap)
+    a = out[: 4 * k].view(k, 4).cpu().numpy()
+    r_, c_, p_ = a[:, 0], a[:, 1], a[:, 2].copy().view(np.float32)
+    top = np.argsort(-p_)[:10000]
+    zs = wl.zmin + wl.zstep * r_[top].astype(np.float64)
+    rs = c_[top].astype(np.float64) / 2.0
+    # 64 injected truths in a fresh series of the same size
+    rng = np.random.default_rng(7)
+    truths = [(float(rng.uniform(2e4, 4e6)), float(rng.uniform(-190, 190)), float(rng.uniform(12, 20)))
+              for _ in range(64)]
+    x = synth.make_series(wl.n, tuple(truths), 77)
+    S.series.copy_(torch.from_numpy(x))
+    S.normalise()
+    r0 = np.array([round(2 * t[0]) / 2 for t in truths])
+    z0 = np.array([2 * round(t[1] / 2) for t in truths])
+    m = fdas_half_width(wl.zmax)
+    r_t = torch.from_numpy(np.concatenate([rs, r0])).to(dev)
+    z_t = torch.from_numpy(np.concatenate([zs, z0])).to(dev)
+    refine(S.spec, r_t, z_t, zmax=wl.zmax, steps=20)      # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r, z, P = refine(S.spec, r_t, z_t, zmax=wl.zmax, steps=20)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    r = r.cpu().numpy()[-64:]
+    z = z.cpu().numpy()[-64:]
+    dr = np.abs(r - np.array([t[0] for t in truths]))
+    dz = np.abs(z - np.array([t[1] for t in truths]))
+    dr0 = np.abs(r0 - np.array([t[0] for t in truths]))
+    dz0 = np.abs(z0 - np.array([t[1] for t in truths]))
+    return {"candidates": int(len(r_t)), "steps": 20, "taps": 2 * m + 1, "ms": ms,
+            "candidate_steps_per_s": len(r_t) * 20 / (ms / 1e3),
+            "truth_err_r": {"median": float(np.median(dr)), "max": float(dr.max()),
+                            "grid_start_median": float(np.median(dr0))},
+            "truth_err_z": {"median": float(np.median(dz)), "max": float(dz.max()),
+                            "grid_start_median": float(np.median(dz0))}}
+
+
 # ----------------------------------------------------------------------------- native leg
 def run_native(args):
     import torch
@@ -333,6 +429,11 @@ def run_native(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clocks,
         }
+        if ws == 1 and not args.no_rows:
+            line["rows"] = {"a11_refine": refine_row(args, torch, dev, S, wl)}
+            del S
+            torch.cuda.empty_cache()
+            line["rows"]["a10_batched"] = batched_row(args, torch, dev)
         if ws == 1 and not args.no_cpu_baseline:
             v, info = oracle_rate(wl, x, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"],
