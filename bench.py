@@ -264,6 +264,47 @@ def batched_row(args, torch, dev):
                       % (ntr, len(bs.waves))}
 
 
+def split_row(args, torch, dev, S, wl):
+    """The production plane with the four radix-16 DFT passes of every segment
+    FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
+    convolver time, and plane and candidate-list differences against the FP32
+    form on the same spectrum (errors against the FP64 oracle come from
+    tests/report_split_error.py)."""
+    S.correlate(fused=True)
+    rf, cf, pf, _, _ = S.candidates()
+    fp32 = {(int(r), int(c)) for r, c in zip(rf, cf)}
+    ref = S.plane.clone()
+    out = {}
+    reps = 10
+    for name, prec in (("fp32", 0), ("fp16_split", 1), ("bf16_split", 2)):
+        for _ in range(3):
+            S.correlate(fused=True, prec=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            S.correlate(fused=True, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r, c, p, _, tot = S.candidates()
+        got = {(int(a), int(b)) for a, b in zip(r, c)}
+        a2 = S.plane.view(S.K, S.row_stride)
+        b2 = ref.view(S.K, S.row_stride)
+        dmax, dsq = 0.0, 0.0
+        for k0 in range(0, S.K, 16):
+            d = (a2[k0:k0 + 16, : S.width] - b2[k0:k0 + 16, : S.width]).abs()
+            dmax = max(dmax, float(d.max()))
+            dsq += float(d.double().square().sum())
+        out[name] = {"conv_ms": ms, "points_per_s": S.K * S.width / (ms / 1e3),
+                     "vs_fp32_plane": {"max_abs": dmax, "rms": (dsq / (S.K * S.width)) ** 0.5},
+                     "candidates": int(tot), "only_here": len(got - fp32),
+                     "only_in_fp32": len(fp32 - got)}
+    del ref
+    return {"workload": "production plane, L=%d" % S.L, "reps": reps, "forms": out,
+            "dft_passes_on_tensor_cores": "radix-16 passes of forward and inverse FFTs "
+                                          "(mma.sync m16n8k16, 3 products per pass)"}
+
+
 def refine_row(args, torch, dev, S, wl):
     """Top 10^4 plane points of the production series plus 64 injected truths,
     20 steps of gradient ascent each."""
@@ -430,7 +471,8 @@ def run_native(args):
             "clocks": clocks,
         }
         if ws == 1 and not args.no_rows:
-            line["rows"] = {"a11_refine": refine_row(args, torch, dev, S, wl)}
+            line["rows"] = {"a9_split": split_row(args, torch, dev, S, wl)}
+            line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()
             line["rows"]["a10_batched"] = batched_row(args, torch, dev)

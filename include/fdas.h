@@ -217,6 +217,34 @@ int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const fl
                    float *plane, int64_t row_stride, const fdas_fused_threshold *fused,
                    int32_t *status, void *stream);
 
+/* Arithmetic of the convolver's radix-16 DFT passes (fdas_correlate_split). */
+#define FDAS_PREC_FP32 0        /* FP32 on the CUDA cores, as fdas_correlate */
+#define FDAS_PREC_FP16_SPLIT 1  /* FP16 hi+lo operands on tensor cores, FP32 accumulation */
+#define FDAS_PREC_BF16_SPLIT 2  /* BF16 hi+lo operands on tensor cores, FP32 accumulation */
+
+/*
+ * fdas_correlate_split -- fdas_correlate with the two radix-16 passes of
+ * every forward and every inverse segment FFT done as matrix products on the
+ * tensor cores (a9).  Section 4.2 writes the DFT as a product with the
+ * Fourier matrix (Eq. matrixDFT) factorised into sparse stages
+ * (Eq. CTfactorization); here one radix-16 stage over 32 segment columns is
+ * the real product Y(32x32) = X(32x32) W(32x32) (re/im interleaved), each
+ * operand split into a 16-bit part and a 16-bit remainder, x = x_hi + x_lo,
+ * W = W_hi + W_lo, with Y = x_hi W_hi + x_hi W_lo + x_lo W_hi accumulated in
+ * FP32 (the lo*lo term is dropped).  The radix-(L/256) pass, the twiddles,
+ * the template product and the powers stay FP32; `bank` is the FP32 bank of
+ * fdas_make_templates.
+ * prec: FDAS_PREC_FP32 (identical to fdas_correlate), FDAS_PREC_FP16_SPLIT
+ *   (parts of 11 significant bits each, 22 together; an intermediate above
+ *   65504 in magnitude overflows to inf) or FDAS_PREC_BF16_SPLIT (8 + 8 bits,
+ *   FP32 range).
+ * Other arguments, layout and errors as fdas_correlate; FDAS_E_INVAL for any
+ * other prec.
+ */
+int fdas_correlate_split(const fdas_params *p, int32_t prec, const float *spec, int64_t nb,
+                         const float *bank, float *plane, int64_t row_stride,
+                         const fdas_fused_threshold *fused, int32_t *status, void *stream);
+
 /*
  * Batched search over many series (a10), e.g. the dispersion trials of one
  * observation, each with its own length: one persistent launch walks the

@@ -16,7 +16,8 @@ __all__ = [
     "params", "fdas_strerror", "fdas_version", "fdas_half_width", "fdas_num_templates",
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
-    "fdas_correlate", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
+    "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
+    "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
@@ -38,6 +39,9 @@ FDAS_STATUS_TIMEOUT = 1
 FDAS_STATUS_OVERFLOW = 2
 FDAS_CAND_PEAK = 1
 FDAS_NOALLOC_MAX_N = 1 << 20
+FDAS_PREC_FP32 = 0
+FDAS_PREC_FP16_SPLIT = 1
+FDAS_PREC_BF16_SPLIT = 2
 
 c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
@@ -101,6 +105,8 @@ def load_library():
         "fdas_normalise_noalloc": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp]),
         "fdas_correlate": (ctypes.c_int, [P(fdas_params), c_vp, c_i64, c_vp, c_vp, c_i64,
                                           P(fdas_fused_threshold), c_vp, c_vp]),
+        "fdas_correlate_split": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
+                                                c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
         "fdas_batch_plan": (c_i64, [P(fdas_params), P(fdas_trial), c_i32]),
@@ -231,6 +237,16 @@ def fdas_correlate(p: fdas_params, spec, nb: int, bank, plane, row_stride: int,
     _check(load_library().fdas_correlate(ctypes.byref(p), _ptr(spec), int(nb), _ptr(bank),
                                          _ptr(plane), int(row_stride), f, _ptr(status),
                                          _stream(stream)), "fdas_correlate")
+
+
+def fdas_correlate_split(p: fdas_params, prec: int, spec, nb: int, bank, plane, row_stride: int,
+                         fused: fdas_fused_threshold | None = None, status=None,
+                         stream=None) -> None:
+    f = ctypes.byref(fused) if fused is not None else None
+    _check(load_library().fdas_correlate_split(ctypes.byref(p), int(prec), _ptr(spec), int(nb),
+                                               _ptr(bank), _ptr(plane), int(row_stride), f,
+                                               _ptr(status), _stream(stream)),
+           "fdas_correlate_split")
 
 
 def fdas_threshold(plane, rows: int, width: int, row_stride: int, thr: float, want_flags: int,

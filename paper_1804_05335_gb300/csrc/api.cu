@@ -99,11 +99,11 @@ int fdas_make_templates(const fdas_params* p, float* bank, void* stream) {
     return launch_templates(p, g, reinterpret_cast<float2*>(bank), (cudaStream_t)stream);
 }
 
-int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const float* bank,
-                   float* plane, int64_t row_stride, const fdas_fused_threshold* fused,
-                   int32_t* status, void* stream) {
-    Grid g;
-    int rc = make_grid(p, &g);
+// Argument checks shared by fdas_correlate and fdas_correlate_split.
+static int check_correlate(const fdas_params* p, Grid* g, const float* spec, int64_t nb,
+                           const float* bank, const float* plane, int64_t row_stride,
+                           const fdas_fused_threshold* fused, const int32_t* status) {
+    int rc = make_grid(p, g);
     if (rc != FDAS_OK) return rc;
     if (!spec || !bank || !plane || nb < 1 || nb > ((int64_t)1 << 31)) return FDAS_E_INVAL;
     if (!aligned(spec, 8) || !aligned(bank, 16) || !aligned(plane, 16)) return FDAS_E_INVAL;
@@ -114,9 +114,35 @@ int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const fl
         if (!aligned(fused->out, 4) || !aligned(fused->count, 4)) return FDAS_E_INVAL;
     }
     if (status && !aligned(status, 4)) return FDAS_E_INVAL;
+    return FDAS_OK;
+}
+
+int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const float* bank,
+                   float* plane, int64_t row_stride, const fdas_fused_threshold* fused,
+                   int32_t* status, void* stream) {
+    Grid g;
+    int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);
+    if (rc != FDAS_OK) return rc;
     return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
                             reinterpret_cast<const float4*>(bank), plane, row_stride, fused,
                             status, (cudaStream_t)stream);
+}
+
+int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, int64_t nb,
+                         const float* bank, float* plane, int64_t row_stride,
+                         const fdas_fused_threshold* fused, int32_t* status, void* stream) {
+    if (prec != FDAS_PREC_FP32 && prec != FDAS_PREC_FP16_SPLIT && prec != FDAS_PREC_BF16_SPLIT)
+        return FDAS_E_INVAL;
+    Grid g;
+    int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);
+    if (rc != FDAS_OK) return rc;
+    if (prec == FDAS_PREC_FP32)
+        return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
+                                reinterpret_cast<const float4*>(bank), plane, row_stride, fused,
+                                status, (cudaStream_t)stream);
+    return launch_correlate_split(p, g, prec, reinterpret_cast<const float2*>(spec), nb,
+                                  reinterpret_cast<const float4*>(bank), plane, row_stride, fused,
+                                  status, (cudaStream_t)stream);
 }
 
 int64_t fdas_batch_plan(const fdas_params* p, fdas_trial* trials, int32_t ntrials) {

@@ -1,430 +1,8 @@
-// fdas_correlate: fused overlap-save convolver (Sections 3, 4.1, 4.2).
-//
-// One persistent CTA per SM slot walks a contiguous, statically balanced
-// range of (segment, template) work items in segment-major order.  For each
-// new segment it loads the L spectrum bins starting at s*B - M/2 (zero
-// outside [0, nb)) and runs the forward FFT once; for every template it
-// multiplies by the template spectrum, runs the inverse FFT, forms full- and
-// half-bin powers of the B useful outputs and writes them to the plane with
-// 16-byte coalesced stores.  Nothing but the plane (and optional candidates)
-// is written to global memory.
-//
-// FFT layout (L = 16*16*Q, T = L/16 threads, 16 complex values per thread):
-// the forward transform is decimation-in-frequency in three register passes
-// (radix 16, 16, Q) separated by shared-memory exchanges, and leaves the
-// spectrum digit-reversed; the inverse is the transposed decimation-in-time
-// sequence (radix Q, 16, 16), which takes digit-reversed input and returns
-// natural order.  The pointwise product therefore never needs the reordering
-// permutation (Section 4.2), and the template bank is stored in the same
-// digit-reversed order.  Thread/register distributions (p = position):
-//   D1: thread t, reg i          p = i*T + t
-//   D2: thread t = a*Q + c, reg b  p = a*T + b*Q + c
-//   D3: thread t = a*Q + c, reg i = s*Q + c2   p = a*T + (c + Q*s)*Q + c2
-// D2 <-> D3 exchanges stay inside a group of Q threads (one warp), D1 <-> D2
-// needs the whole CTA.  Both shared-memory layouts are padded so that every
-// exchange is free of bank conflicts.
-//
-// z < 0 templates of a symmetric grid use H_{-z}[k] = conj(H_z[-k mod L])
-// (Section 4.2): in D3, -k of (thread t, reg i) lives in (partner(t), 15-i)
-// except for thread 0, handled separately.
-#include <algorithm>
-
-#include "conv_fft.cuh"
-#include "internal.h"
-#include "tma.cuh"
+// fdas_correlate and fdas_correlate_batched: launchers of the FP32 convolver
+// (kernel in conv_kernel.cuh).
+#include "conv_kernel.cuh"
 
 namespace fdas {
-
-struct ConvArgs {
-    const float2* spec;
-    int64_t nb;
-    const float4* bank;
-    float* plane;
-    int64_t row_stride;
-    int64_t items;      // nseg * K
-    int32_t K;
-    int32_t j0;
-    int32_t sym;
-    int32_t zero;
-    int32_t M;
-    int32_t interbin;
-    float thr;
-    fdas_cand* cand;
-    int32_t cap;
-    int32_t* count;
-    int32_t* status;
-    const fdas_trial* trials;   // batched launches: device table of ntrials series
-    int32_t ntrials;
-};
-
-template <int L>
-struct ConvSmem {
-    using S = ConvShape<L>;
-    static constexpr int TW3 = 16 * (S::Q + 1);
-    // buf0 | buf1 | outb (L) | hbuf (bank row) | tw3
-    static constexpr size_t bytes = (size_t)(2 * S::BUFS + L + S::ROW + TW3) * sizeof(float2);
-};
-
-// polls of the template-row bulk copy before the kernel gives up
-constexpr uint32_t kWaitLimit = 1u << 22;
-
-__device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, float v, int flags) {
-    int idx = atomicAdd(A.count, 1);
-    if (idx < A.cap) {
-        fdas_cand c;
-        c.z_idx = row;
-        c.col = (int32_t)col;
-        c.power = v;
-        c.flags = flags;
-        A.cand[idx] = c;
-    } else if (A.status) {
-        atomicOr(A.status, FDAS_STATUS_OVERFLOW);
-    }
-}
-
-// Template of item q inside a segment: bank row, plane row, conjugation.
-// Items of a symmetric grid pair +z with -z so that both use one bank row.
-__device__ __forceinline__ void item_row(const ConvArgs& A, int q, int& row, int& brow, int& cj) {
-    if (!A.sym) {
-        row = q; brow = q; cj = 0;
-        return;
-    }
-    if (A.zero) {
-        if (q == 0) { brow = 0; cj = 0; }
-        else { brow = (q + 1) >> 1; cj = (q & 1) ? 0 : 1; }
-    } else {
-        brow = q >> 1; cj = q & 1;
-    }
-    row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
-}
-
-// Powers of one pair of positions (j, j+1) given x[j], x[j+1], x[j+2].
-__device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
-    const float hs = 0.61685027506808491f;   // (pi/4)^2
-    const float dx0 = x01.x - x01.z, dy0 = x01.y - x01.w;
-    const float dx1 = x01.z - xn.x, dy1 = x01.w - xn.y;
-    return make_float4(fmaf(x01.x, x01.x, x01.y * x01.y), hs * fmaf(dx0, dx0, dy0 * dy0),
-                       fmaf(x01.z, x01.z, x01.w * x01.w), hs * fmaf(dx1, dx1, dy1 * dy1));
-}
-
-// Series state of the item being processed: one series for fdas_correlate,
-// the trial table entry for fdas_correlate_batched.
-struct SeriesState {
-    const float2* spec;
-    int64_t nb;
-    float* plane;
-    int64_t row_stride;
-    int64_t end;   // first item of the next series
-    int flags;     // candidate flags: trial index << 8 in batched launches
-};
-
-template <bool BATCH>
-__device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
-    SeriesState st;
-    if constexpr (BATCH) {
-        const fdas_trial& tr = A.trials[trial];
-        st.spec = reinterpret_cast<const float2*>(tr.spec);
-        st.nb = tr.nb;
-        st.plane = tr.plane;
-        st.row_stride = tr.row_stride;
-        st.end = (trial + 1 < A.ntrials) ? A.trials[trial + 1].item_begin : A.items;
-        st.flags = trial << 8;
-    } else {
-        st.spec = A.spec;
-        st.nb = A.nb;
-        st.plane = A.plane;
-        st.row_stride = A.row_stride;
-        st.end = A.items;
-        st.flags = 0;
-    }
-    return st;
-}
-
-template <int L, bool FUSE, bool BATCH>
-__global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const ConvArgs A) {
-    using S = ConvShape<L>;
-    constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
-    extern __shared__ float4 smem4[];
-    float2* buf0 = reinterpret_cast<float2*>(smem4);
-    float2* buf1 = buf0 + BUFS;
-    float2* outb = buf1 + BUFS;
-    float2* hbuf = outb + L;
-    float2* tw3 = hbuf + S::ROW;
-    __shared__ uint64_t hbar;
-
-    const int t = threadIdx.x;
-    const int a = t / Q, c = t % Q;
-    const int M = A.M, B = L - M, NP = B / 2;
-
-    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
-    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
-    if (lo >= hi) return;
-    int trial = 0;
-    if constexpr (BATCH) {
-        // last trial whose first item is <= lo
-        int a0 = 0, a1 = A.ntrials - 1;
-        while (a0 < a1) {
-            const int mid = (a0 + a1 + 1) >> 1;
-            if (A.trials[mid].item_begin <= lo) a0 = mid; else a1 = mid - 1;
-        }
-        trial = a0;
-    }
-    SeriesState st = series_of<BATCH>(A, trial);
-    const int64_t first = BATCH ? A.trials[trial].item_begin : 0;
-    int64_t s = (lo - first) / A.K;
-    int q = (int)(lo - first - s * A.K);
-    int row, brow, cj;
-    item_row(A, q, row, brow, cj);
-
-    if (t == 0) {
-        mbar_init(&hbar, 1);
-        tma_load_1d(hbuf, A.bank + (size_t)brow * (S::ROW / 2), S::ROW * sizeof(float2), &hbar);
-    }
-    // inverse pass-3' twiddles: tw3[k1*(Q+1) + n2] = exp(+i 2 pi n2 k1 / (L/16))
-    for (int idx = t; idx < ConvSmem<L>::TW3; idx += T) {
-        int k1 = idx / (Q + 1), n2 = idx % (Q + 1);
-        float sn, cs;
-        sincospif(2.0f * (float)((n2 * k1) % (L / 16)) / (float)(L / 16), &sn, &cs);
-        tw3[idx] = make_float2(cs, sn);
-    }
-    // inverse pass-2' twiddles (thread (a, c), reg n1): exp(+i 2 pi (n1 Q + c) a / L)
-    float2 tw2[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        float sn, cs;
-        sincospif(2.0f * (float)(((n1 * Q + c) * a) % L) / (float)L, &sn, &cs);
-        tw2[n1] = make_float2(cs, sn);
-    }
-    // conjugate (z < 0) templates read H[-k]: float4 pair ip of this thread
-    // sits at hbase - ip*hstep, halves swapped (partner thread, reversed
-    // registers); thread 0 reads the mirror slots at the end of the row.
-    const int tp = (a != 0) ? (16 - a) * Q + (Q - 1 - c) : (Q - c) % Q;
-    const int hbase = (t == 0) ? L / 2 + 7 : 7 * T + tp;
-    const int hstep = (t == 0) ? 1 : T;
-    __syncthreads();
-
-    int64_t cur_seg = -1;
-    int parity = 0;
-    uint32_t hphase = 0;
-    bool hpending = true;
-    float2 Y[16];
-    float2 v[16];
-    const float4* hb4 = reinterpret_cast<const float4*>(hbuf);
-
-    for (int64_t w = lo; w < hi; ++w) {
-        if constexpr (BATCH) {
-            if (w == st.end) {   // next trial: its first segment and template
-                ++trial;
-                st = series_of<BATCH>(A, trial);
-                s = 0;
-                q = 0;
-                cur_seg = -1;
-            }
-        }
-        if (s != cur_seg) {
-            // ---- forward FFT of segment s, once per segment ----
-            cur_seg = s;
-            const int64_t base = s * (int64_t)B - M / 2;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t pos = base + i * T + t;
-                v[i] = (pos >= 0 && pos < st.nb) ? __ldg(&st.spec[pos]) : make_float2(0.f, 0.f);
-            }
-            forward_fft_d3<L>(v, buf0, buf1, t);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) Y[i] = v[i];
-            __syncthreads();   // exchange buffers free again
-            parity = 0;
-        }
-
-        // ---- multiply by the template spectrum staged in shared memory ----
-        bool tmo = false;
-        if (hpending) {
-            tmo = !mbar_wait_bounded(&hbar, hphase, kWaitLimit);
-            hphase ^= 1u;
-            hpending = false;
-        }
-        if (!cj) {
-#pragma unroll
-            for (int ip = 0; ip < 8; ++ip) {
-                const float4 h = hb4[ip * T + t];
-                v[2 * ip] = cmul(Y[2 * ip], make_float2(h.x, h.y));
-                v[2 * ip + 1] = cmul(Y[2 * ip + 1], make_float2(h.z, h.w));
-            }
-        } else {
-#pragma unroll
-            for (int ip = 0; ip < 8; ++ip) {
-                const float4 h = hb4[hbase - ip * hstep];
-                v[2 * ip] = cmulc(Y[2 * ip], make_float2(h.z, h.w));
-                v[2 * ip + 1] = cmulc(Y[2 * ip + 1], make_float2(h.x, h.y));
-            }
-        }
-
-        // ---- inverse pass 3': radix Q over k2, then twiddle ----
-#pragma unroll
-        for (int s2 = 0; s2 < NS; ++s2) {
-            dftq<Q, 1>(v + s2 * Q);
-#pragma unroll
-            for (int n2 = 1; n2 < Q; ++n2)
-                v[s2 * Q + n2] = cmul(v[s2 * Q + n2], tw3[(c + Q * s2) * (Q + 1) + n2]);
-        }
-        // ---- D3 -> D2 inside the Q-thread group ----
-        {
-            float2* x2 = (parity ? buf0 : buf1) + a * G;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) x2[(c + Q * (i / Q)) * (Q + 1) + (i % Q)] = v[i];
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = x2[i * (Q + 1) + c];
-        }
-        // ---- inverse pass 2': radix 16 over k1, then twiddle ----
-        dft16<1>(v);
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = cmul(v[n1], tw2[n1]);
-        // ---- D2 -> D1 across the CTA ----
-        float2* x1 = parity ? buf1 : buf0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) x1[a * (T + Q) + i * Q + c] = v[i];
-        if (__syncthreads_or(tmo)) {
-            if (t == 0 && A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
-            break;
-        }
-
-        // ---- next item; prefetch its template row if it changes ----
-        const int64_t s_next = (q + 1 == A.K) ? s + 1 : s;
-        const int q_next = (q + 1 == A.K) ? 0 : q + 1;
-        int row_n = 0, brow_n = brow, cj_n = 0;
-        if (w + 1 < hi) {
-            item_row(A, q_next, row_n, brow_n, cj_n);
-            if (brow_n != brow) {
-                if (t == 0) {
-                    fence_proxy_async();
-                    tma_load_1d(hbuf, A.bank + (size_t)brow_n * (S::ROW / 2), S::ROW * sizeof(float2),
-                                &hbar);
-                }
-                hpending = true;
-            }
-        }
-
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = x1[i * (T + Q) + t];
-        // ---- inverse pass 1': radix 16 over k0 -> natural order ----
-        dft16<1>(v);
-#pragma unroll
-        for (int n0 = 0; n0 < 16; ++n0) outb[n0 * T + t] = v[n0];
-        __syncthreads();
-
-        // ---- epilogue: powers of positions M/2 .. M/2+B, two bins per pair ----
-        const int64_t r0 = s * (int64_t)B;
-        float* prow = st.plane + (int64_t)row * st.row_stride;
-        const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
-        const float2* o2 = outb + M / 2 + 2;
-        float mx = 0.f;
-        if (r0 + B < st.nb) {
-            constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
-            if (A.interbin) {
-                float4* dst = reinterpret_cast<float4*>(prow + 2 * r0);
-#pragma unroll
-                for (int u = 0; u < UMAX; ++u) {
-                    const int p = t + u * T;
-                    if (p < NP) {
-                        const float4 pw = pair_powers(o4[p], o2[2 * p]);
-                        __stcs(dst + p, pw);
-                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
-                    }
-                }
-            } else {
-                float2* dst = reinterpret_cast<float2*>(prow + r0);
-#pragma unroll
-                for (int u = 0; u < UMAX; ++u) {
-                    const int p = t + u * T;
-                    if (p < NP) {
-                        const float4 x = o4[p];
-                        const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
-                        __stcs(dst + p, pw);
-                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
-                    }
-                }
-            }
-        } else {
-            // segment reaching the end of the spectrum: per-bin checks
-            for (int p = t; p < NP; p += T) {
-                const int64_t r = r0 + 2 * p;
-                if (r >= st.nb) break;
-                float4 pw = pair_powers(o4[p], o2[2 * p]);
-                if (r + 1 >= st.nb - 1) pw.w = 0.f;       // no bin r+2
-                if (r >= st.nb - 1) pw.y = 0.f;           // no bin r+1
-                if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
-                if (A.interbin) {
-                    prow[2 * r] = pw.x;
-                    prow[2 * r + 1] = pw.y;
-                    if (r + 1 < st.nb) { prow[2 * r + 2] = pw.z; prow[2 * r + 3] = pw.w; }
-                } else {
-                    prow[r] = pw.x;
-                    if (r + 1 < st.nb) prow[r + 1] = pw.z;
-                    pw.y = 0.f;
-                    pw.w = 0.f;
-                }
-                if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
-            }
-        }
-        if constexpr (FUSE) {
-            if (mx > A.thr) {
-                // rare: rescan this thread's pairs and emit each crossing
-                for (int p = t; p < NP; p += T) {
-                    const int64_t r = r0 + 2 * p;
-                    if (r >= st.nb) break;
-                    float4 pw = pair_powers(o4[p], o2[2 * p]);
-                    if (r + 1 >= st.nb - 1) pw.w = 0.f;
-                    if (r >= st.nb - 1) pw.y = 0.f;
-                    if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
-                    if (A.interbin) {
-                        if (pw.x > A.thr) emit(A, row, 2 * r, pw.x, st.flags);
-                        if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y, st.flags);
-                        if (pw.z > A.thr) emit(A, row, 2 * r + 2, pw.z, st.flags);
-                        if (pw.w > A.thr) emit(A, row, 2 * r + 3, pw.w, st.flags);
-                    } else {
-                        if (pw.x > A.thr) emit(A, row, r, pw.x, st.flags);
-                        if (pw.z > A.thr) emit(A, row, r + 1, pw.z, st.flags);
-                    }
-                }
-            }
-        }
-        parity ^= 1;
-        s = s_next;
-        q = q_next;
-        row = row_n;
-        brow = brow_n;
-        cj = cj_n;
-    }
-}
-
-template <int L, bool FUSE, bool BATCH>
-static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
-    using S = ConvShape<L>;
-    constexpr size_t smem = ConvSmem<L>::bytes;
-    static int sms = 0, max_per_sm = 0;
-    if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return FDAS_E_CUDA;
-        int dev = 0, n = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH>,
-                                                          S::T, smem) != cudaSuccess)
-            return FDAS_E_CUDA;
-        if (per_sm < 1) return FDAS_E_UNSUPPORTED;
-        max_per_sm = per_sm;
-        sms = n;
-    }
-    const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
-    const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
-    conv_kernel<L, FUSE, BATCH><<<(unsigned)g, S::T, smem, st>>>(args);
-    return cuda_status(cudaGetLastError());
-}
 
 template <bool BATCH>
 static int dispatch(const fdas_params* p, const ConvArgs& a, bool fused, int ctas_per_sm,
@@ -442,31 +20,6 @@ static int dispatch(const fdas_params* p, const ConvArgs& a, bool fused, int cta
         default:
             return FDAS_E_INVAL;
     }
-}
-
-static ConvArgs base_args(const fdas_params* p, const Grid& g, const float4* bank,
-                          const fdas_fused_threshold* fused, int32_t* status) {
-    ConvArgs a;
-    a.spec = nullptr;
-    a.nb = 0;
-    a.plane = nullptr;
-    a.row_stride = 0;
-    a.items = 0;
-    a.bank = bank;
-    a.K = g.K;
-    a.j0 = g.j0;
-    a.sym = g.sym;
-    a.zero = g.zero;
-    a.M = p->M;
-    a.interbin = p->interbin;
-    a.thr = fused ? fused->thr : 0.f;
-    a.cand = fused ? fused->out : nullptr;
-    a.cap = fused ? fused->cap : 0;
-    a.count = fused ? fused->count : nullptr;
-    a.status = status;
-    a.trials = nullptr;
-    a.ntrials = 0;
-    return a;
 }
 
 int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,

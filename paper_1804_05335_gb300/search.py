@@ -11,7 +11,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (fdas_bank_floats, fdas_bank_rows, fdas_correlate, fdas_fused_threshold, fdas_make_templates,
+from . import (fdas_bank_floats, fdas_bank_rows, fdas_correlate, fdas_correlate_split,
+               fdas_fused_threshold, fdas_make_templates,
                fdas_normalise, fdas_normalise_workspace_bytes, fdas_num_segments,
                fdas_num_templates, fdas_plane_width, fdas_threshold, params)
 
@@ -55,10 +56,15 @@ class Search:
         fdas_normalise(self.series, self.n, self.median_block, self.spec, self.work,
                        self.work_bytes, stream)
 
-    def correlate(self, fused: bool = True, spec=None, nb=None, stream=None):
-        fdas_correlate(self.p, self.spec if spec is None else spec,
-                       self.nb if nb is None else nb, self.bank, self.plane, self.row_stride,
-                       self.fused if fused else None, self.status, stream)
+    def correlate(self, fused: bool = True, spec=None, nb=None, stream=None, prec: int = 0):
+        """The plane (and fused candidates); prec selects the DFT arithmetic
+        (FDAS_PREC_*: 0 = FP32, 1 / 2 = FP16 / BF16 split tensor-core passes)."""
+        args = (self.spec if spec is None else spec, self.nb if nb is None else nb, self.bank,
+                self.plane, self.row_stride, self.fused if fused else None, self.status, stream)
+        if prec == 0:
+            fdas_correlate(self.p, *args)
+        else:
+            fdas_correlate_split(self.p, prec, *args)
 
     def threshold(self, want_peaks: bool = True, stream=None):
         fdas_threshold(self.plane, self.K, self.width, self.row_stride, self.thr,
