@@ -91,7 +91,7 @@ def measured_peak():
 
 def conv_source_sha():
     h = hashlib.sha256()
-    for f in ("convolve.cu", "dft.cuh"):
+    for f in ("conv_kernel.cuh", "conv_fft.cuh", "dft.cuh", "tma.cuh", "convolve.cu"):
         with open(os.path.join(ROOT, "paper_1804_05335_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
