@@ -66,6 +66,28 @@ def dist_setup():
     return ws, rank, local
 
 
+def rank_seed(seed, rank):
+    """Each rank searches its own series (an independent dispersion trial):
+    the workload's seed offset by the rank."""
+    return seed + rank
+
+
+def max_over_ranks(value, ws, device):
+    """The largest of the ranks' values (every rank gets it)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(ws, units_per_rank, steps, total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return ws * units_per_rank * steps / (total_ms / 1e3)
+
+
 def workload(args):
     wl = synth.workload(args.workload)
     if args.L:
@@ -372,7 +394,7 @@ def run_native(args):
     from paper_1804_05335_gb300.search import Search
 
     wl = workload(args)
-    x = synth.make_series(wl.n, wl.injections, wl.seed + rank)
+    x = synth.make_series(wl.n, wl.injections, rank_seed(wl.seed, rank))
     S = Search(wl.n, wl.L, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
                median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
     host_series = torch.from_numpy(x).pin_memory()
@@ -414,12 +436,9 @@ def run_native(args):
     step_ms = [a.elapsed_time(c) for a, _, c, _ in evs]
     conv_ms = [b.elapsed_time(c) for _, b, c, _ in evs]
     tpl_ms = [a.elapsed_time(d) for a, _, _, d in evs]
-    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(total, op=dist.ReduceOp.MAX)
-    total_ms = float(total.item())
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * points * args.steps / (total_ms / 1e3)
+    value = aggregate_rate(ws, points, args.steps, total_ms)
 
     # end to end: host series -> device, the step, candidates -> host
     cand_host = torch.empty(1 + 4 * S.cap, dtype=torch.int32).pin_memory()
@@ -435,10 +454,8 @@ def run_native(args):
         cand_host[1:].copy_(S.cand, non_blocking=True)
     s1.record()
     torch.cuda.synchronize()
-    e2e_t = torch.tensor([s0.elapsed_time(s1)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * points * args.e2e_steps / (float(e2e_t.item()) / 1e3)
+    e2e_value = aggregate_rate(ws, points, args.e2e_steps,
+                               max_over_ranks(s0.elapsed_time(s1), ws, dev))
     n_cand = int(cand_host[0].item())
 
     if rank == 0:
