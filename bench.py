@@ -447,11 +447,9 @@ def run_native(args):
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record()
-    for _ in range(args.e2e_steps):
-        S.series.copy_(host_series, non_blocking=True)
-        S.step()
-        cand_host[:1].copy_(S.count, non_blocking=True)
-        cand_host[1:].copy_(S.cand, non_blocking=True)
+    # the public streaming call: each series copied in from pinned host memory
+    # (overlapping the previous search), searched, its candidates copied out
+    S.stream([host_series] * args.e2e_steps, [cand_host] * args.e2e_steps)
     s1.record()
     torch.cuda.synchronize()
     e2e_value = aggregate_rate(ws, points, args.e2e_steps,

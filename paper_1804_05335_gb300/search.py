@@ -52,9 +52,9 @@ class Search:
     def make_templates(self, stream=None):
         fdas_make_templates(self.p, self.bank, stream)
 
-    def normalise(self, stream=None):
-        fdas_normalise(self.series, self.n, self.median_block, self.spec, self.work,
-                       self.work_bytes, stream)
+    def normalise(self, stream=None, series=None):
+        fdas_normalise(self.series if series is None else series, self.n, self.median_block,
+                       self.spec, self.work, self.work_bytes, stream)
 
     def correlate(self, fused: bool = True, spec=None, nb=None, stream=None, prec: int = 0):
         """The plane (and fused candidates); prec selects the DFT arithmetic
@@ -71,11 +71,44 @@ class Search:
                        1 if want_peaks else 0, self.cand, self.cap, self.count, self.status,
                        stream)
 
-    def step(self, stream=None):
+    def step(self, stream=None, series=None):
         """One pass of the hot path: bank, spectrum, plane + fused candidates."""
         self.make_templates(stream)
-        self.normalise(stream)
+        self.normalise(stream, series)
         self.correlate(True, stream=stream)
+
+    def stream(self, host_series, host_out):
+        """Search the pinned host series host_series[i] (n float32 each) one
+        after another on the current CUDA stream, copying series i+1 to the
+        device on a second stream while series i is searched.  The candidate
+        count and list of series i land in the pinned int32 tensor host_out[i]
+        (1 + 4*cap values: count, then (row, col, power bits, flags) per
+        candidate); entries may alias when only the last result is wanted.
+        Returns once everything is queued; synchronise before reading host_out."""
+        main = torch.cuda.current_stream(self.device)
+        if not hasattr(self, "_copy"):
+            self._copy = torch.cuda.Stream(self.device)
+            self._inbuf = [self.series, torch.empty_like(self.series)]
+        loaded = [torch.cuda.Event(), torch.cuda.Event()]
+        start = torch.cuda.Event()
+        start.record(main)                 # earlier work on the input buffers
+        self._copy.wait_event(start)
+        free = [None, None]
+        for i, hs in enumerate(host_series):
+            j = i & 1
+            with torch.cuda.stream(self._copy):
+                if free[j] is not None:
+                    self._copy.wait_event(free[j])   # series i-2 has been read
+                self._inbuf[j].copy_(hs, non_blocking=True)
+                loaded[j].record(self._copy)
+            main.wait_event(loaded[j])
+            self.make_templates()
+            self.normalise(series=self._inbuf[j])
+            free[j] = torch.cuda.Event()
+            free[j].record(main)
+            self.correlate(True)
+            host_out[i][:1].copy_(self.count, non_blocking=True)
+            host_out[i][1:].copy_(self.cand, non_blocking=True)
 
     # ---- views ----
     def plane2d(self) -> torch.Tensor:
