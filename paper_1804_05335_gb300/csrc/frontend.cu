@@ -10,8 +10,9 @@
 //   pass B: length-N2 DFTs over n2, twiddle exp(-i 2 pi n1 k2 / (N1 N2));
 //   pass C: length-N1 DFTs over n1, written transposed to natural order.
 // Each pass moves tiles of 16 lines x R points through shared memory with
-// 128-byte coalesced rows and runs a radix-2 Stockham (self-sorting) DFT on
-// the tile.  A final kernel per median block forms the real spectrum
+// 128-byte coalesced rows and transforms each line by two register passes,
+// R = R1 x 16: radix R1 over every 16th point, a twiddle, one padded
+// transpose in shared memory, radix 16 (tile_dft).  A final kernel per median block forms the real spectrum
 //   X_k = E_k + exp(-i 2 pi k / n) O_k,  E = (Z_k + conj Z_{N-k})/2,
 //   O = (Z_k - conj Z_{N-k}) / 2i,   X_0 := 0,
 // selects the lower median of |X_k|^2 in the block exactly (radix select on
@@ -20,6 +21,7 @@
 
 #include <mutex>
 
+#include "dft.cuh"
 #include "internal.h"
 
 namespace fdas {
@@ -27,36 +29,66 @@ namespace fdas {
 constexpr int kFeThreads = 256;
 constexpr int kTilePad = 17;   // tile row stride in float2 (16 lines + 1)
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Forward length-R DFT of the 16 columns of tile x[r*17 + col]; returns the
-// buffer that holds the result (x or y).  tw[q] = exp(-i 2 pi q / R), q < R/2.
-__device__ float2* tile_dft(float2* x, float2* y, const float2* tw, int R) {
-    const int nb = 8 * R;   // butterflies per stage over 16 columns
-    for (int l = R / 2, m = 1; l >= 1; l >>= 1, m <<= 1) {
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int col = b & 15, bf = b >> 4;
-            const int j = bf / m, k = bf - j * m;
-            const float2 w = tw[j * m];
-            const float2 c0 = x[(k + j * m) * kTilePad + col];
-            const float2 c1 = x[(k + j * m + l * m) * kTilePad + col];
-            y[(k + 2 * j * m) * kTilePad + col] = c_add(c0, c1);
-            y[(k + 2 * j * m + m) * kTilePad + col] = c_mul(w, c_sub(c0, c1));
+// Forward length-R DFT (R = R1*16) of the 16 columns of tile x[r*17 + col].
+// Thread (col = t % 16, j = t / 16) takes points r = j + 16 i, i < R1, does
+// the radix-R1 DFT over i, multiplies output k1 by exp(-i 2 pi j k1 / R) and
+// stores it at y[(16 k1 + j)*17 + col]; thread (col, k1) then does the
+// radix-16 DFT over j and writes frequency k = k1 + R1 k2 to x[k*17 + col].
+// Every access pattern touches each bank pair at most twice per warp.
+// tw[q] = exp(-i 2 pi q / R), q < R.  Ends with a barrier; returns x.
+template <int R1>
+__device__ void tile_dft_r(float2* x, float2* y, const float2* tw) {
+    constexpr int R = 16 * R1;
+    const int t = threadIdx.x, col = t & 15, jj = t >> 4;
+    float2 v[16];
+    if constexpr (R1 > 1) {
+#pragma unroll
+        for (int i = 0; i < R1; ++i) v[i] = x[(jj + 16 * i) * kTilePad + col];
+        if constexpr (R1 == 2) {
+            dft2<-1>(v[0], v[1]);
+        } else if constexpr (R1 == 4) {
+            dft4<-1>(v[0], v[1], v[2], v[3]);
+        } else if constexpr (R1 == 8) {
+            dft8<-1>(v);
+        } else {
+            dft16<-1>(v);
         }
-        __syncthreads();
-        float2* t = x;
-        x = y;
-        y = t;
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) v[k1] = c_mul(v[k1], tw[jj * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) y[(16 * k1 + jj) * kTilePad + col] = v[k1];
+    } else {
+        y[jj * kTilePad + col] = x[jj * kTilePad + col];
+    }
+    __syncthreads();
+    if (jj < R1) {
+        const int k1 = jj;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = y[(16 * k1 + j) * kTilePad + col];
+        dft16<-1>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) x[(k1 + R1 * k2) * kTilePad + col] = v[k2];
+    }
+    __syncthreads();
+}
+
+__device__ float2* tile_dft(float2* x, float2* y, const float2* tw, int R) {
+    switch (R) {
+        case 16: tile_dft_r<1>(x, y, tw); break;
+        case 32: tile_dft_r<2>(x, y, tw); break;
+        case 64: tile_dft_r<4>(x, y, tw); break;
+        case 128: tile_dft_r<8>(x, y, tw); break;
+        default: tile_dft_r<16>(x, y, tw); break;
     }
     return x;
 }
 
 __device__ void load_tw(float2* tw, int R) {
-    for (int q = threadIdx.x; q < R / 2; q += blockDim.x) {
+    for (int q = threadIdx.x; q < R; q += blockDim.x) {
         float s, c;
         sincospif(2.0f * (float)q / (float)R, &s, &c);
         tw[q] = make_float2(c, -s);
@@ -76,7 +108,7 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict
                                                         int64_t N12, int64_t N) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 128;
+    float2* x = tw + 256;
     float2* y = x + 256 * kTilePad;
     const int64_t m0 = (int64_t)blockIdx.x * 16;
     load_tw(tw, N3);
@@ -97,7 +129,7 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict
 __global__ void __launch_bounds__(kFeThreads) fe_pass_b(float2* __restrict__ buf, int N1, int N2) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 128;
+    float2* x = tw + 256;
     float2* y = x + 256 * kTilePad;
     const int chunks = N1 / 16;
     const int64_t k3 = blockIdx.x / chunks;
@@ -125,7 +157,7 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_c(const float2* __restrict
                                                         int N3) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 128;
+    float2* x = tw + 256;
     float2* y = x + 256 * kTilePad;
     const int chunks = N3 / 16;
     const int64_t k2 = blockIdx.x / chunks;
@@ -259,7 +291,7 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
     const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
     const int64_t N12 = (int64_t)N1 * N2;
-    const size_t tile_sm = (128 + 2 * 256 * kTilePad) * sizeof(float2);
+    const size_t tile_sm = (256 + 2 * 256 * kTilePad) * sizeof(float2);
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(fe_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
