@@ -109,10 +109,10 @@ __device__ __forceinline__ void item_row(const ConvArgs& A, int q, int& row, int
 // Powers of one pair of positions (j, j+1) given x[j], x[j+1], x[j+2].
 __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
     const float hs = 0.61685027506808491f;   // (pi/4)^2
-    const float dx0 = x01.x - x01.z, dy0 = x01.y - x01.w;
-    const float dx1 = x01.z - xn.x, dy1 = x01.w - xn.y;
-    return make_float4(fmaf(x01.x, x01.x, x01.y * x01.y), hs * fmaf(dx0, dx0, dy0 * dy0),
-                       fmaf(x01.z, x01.z, x01.w * x01.w), hs * fmaf(dx1, dx1, dy1 * dy1));
+    const float2 x0 = make_float2(x01.x, x01.y), x1 = make_float2(x01.z, x01.w);
+    const float2 d0 = x0 - x1, d1 = x1 - xn;
+    return make_float4(fmaf(x0.x, x0.x, x0.y * x0.y), hs * fmaf(d0.x, d0.x, d0.y * d0.y),
+                       fmaf(x1.x, x1.x, x1.y * x1.y), hs * fmaf(d1.x, d1.x, d1.y * d1.y));
 }
 
 // Series state of the item being processed: one series for fdas_correlate,

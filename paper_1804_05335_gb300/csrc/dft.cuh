@@ -3,13 +3,20 @@
 // S = +1 the inverse without 1/N  (DFT and IDFT of Section 4.2).  Inputs and
 // outputs are in natural order; all indices are compile-time constants so
 // the permutations are register renames.
+//
+// A complex value is a float2 (re, im) in an aligned register pair, so a
+// complex addition is one packed FADD2 (sm_100+), the same IEEE addition per
+// component.  Products by +-i cross the components and stay scalar, folded
+// into the additions that consume them.
 #pragma once
 #include <cuda_runtime.h>
 
 namespace fdas {
 
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
 
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -23,6 +30,15 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 template <int S>
 __device__ __forceinline__ float2 mul_si(float2 v) {
     return S > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+// a + S i b  and  a - S i b
+template <int S>
+__device__ __forceinline__ float2 add_si(float2 a, float2 b) {
+    return S > 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <int S>
+__device__ __forceinline__ float2 sub_si(float2 a, float2 b) {
+    return S > 0 ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
 }
 
 constexpr float kC8 = 0.92387953251128674f;  // cos(pi/8)
@@ -70,12 +86,21 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
 
 template <int S>
 __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-    float2 s02 = x0 + x2, d02 = x0 - x2, s13 = x1 + x3;
-    float2 d13 = mul_si<S>(x1 - x3);
+    const float2 s02 = x0 + x2, d02 = x0 - x2, s13 = x1 + x3, d13 = x1 - x3;
     x0 = s02 + s13;
     x2 = s02 - s13;
-    x1 = d02 + d13;
-    x3 = d02 - d13;
+    x1 = add_si<S>(d02, d13);
+    x3 = sub_si<S>(d02, d13);
+}
+
+// dft4 of (x0, x1, S i x2, x3): the factor on x2 folded into its additions
+template <int S>
+__device__ __forceinline__ void dft4_r2(float2& x0, float2& x1, float2& x2, float2& x3) {
+    const float2 s02 = add_si<S>(x0, x2), d02 = sub_si<S>(x0, x2), s13 = x1 + x3, d13 = x1 - x3;
+    x0 = s02 + s13;
+    x2 = s02 - s13;
+    x1 = add_si<S>(d02, d13);
+    x3 = sub_si<S>(d02, d13);
 }
 
 // 8 points: n = 2 n1 + n2, k = k1 + 4 k2
@@ -84,11 +109,14 @@ __device__ __forceinline__ void dft8(float2* v) {
     dft4<S>(v[0], v[2], v[4], v[6]);
     dft4<S>(v[1], v[3], v[5], v[7]);
     v[3] = w16<S, 2>(v[3]);
-    v[5] = w16<S, 4>(v[5]);
     v[7] = w16<S, 6>(v[7]);
     dft2<S>(v[0], v[1]);
     dft2<S>(v[2], v[3]);
-    dft2<S>(v[4], v[5]);
+    {   // (v4, S i v5)
+        const float2 t = sub_si<S>(v[4], v[5]);
+        v[4] = add_si<S>(v[4], v[5]);
+        v[5] = t;
+    }
     dft2<S>(v[6], v[7]);
     // X[k1 + 4 k2] sits in v[2 k1 + k2]
     float2 t1 = v[1], t2 = v[2], t3 = v[3], t4 = v[4], t5 = v[5], t6 = v[6];
@@ -109,13 +137,14 @@ __device__ __forceinline__ void dft16(float2* v) {
     v[6] = w16<S, 2>(v[6]);
     v[7] = w16<S, 3>(v[7]);
     v[9] = w16<S, 2>(v[9]);
-    v[10] = w16<S, 4>(v[10]);
     v[11] = w16<S, 6>(v[11]);
     v[13] = w16<S, 3>(v[13]);
     v[14] = w16<S, 6>(v[14]);
     v[15] = w16<S, 9>(v[15]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    dft4<S>(v[0], v[1], v[2], v[3]);
+    dft4<S>(v[4], v[5], v[6], v[7]);
+    dft4_r2<S>(v[8], v[9], v[10], v[11]);   // v[10] carries w16^4 = S i
+    dft4<S>(v[12], v[13], v[14], v[15]);
     // X[k1 + 4 k2] sits in v[4 k1 + k2]: transpose the 4x4
     float2 t;
     t = v[1]; v[1] = v[4]; v[4] = t;
