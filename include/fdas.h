@@ -53,7 +53,12 @@ extern "C" {
  *           Fig. 1: blocks of L = B + M points).
  *  M        padded template width in taps: a multiple of 4 with
  *           64 <= M <= L/2; each segment yields B = L - M useful bins and
- *           the longest template must fit: h(max|z|) <= M/2 - 1.
+ *           the longest template must fit: h(max|z|) <= M/2 - 1.  M is the
+ *           largest overlap used: on a symmetric grid the convolver splits
+ *           the templates into up to FDAS_MAX_GROUPS groups of increasing |z|
+ *           and gives each group the smallest overlap its longest template
+ *           needs (fdas_template_groups); the overlap only moves segment
+ *           boundaries, not the correlation values.
  *  zmin, zmax, zstep
  *           template grid z_j = zmin + j*zstep, j = 0..K-1,
  *           K = (zmax - zmin)/zstep + 1; zstep >= 1, (zmax - zmin) % zstep == 0.
@@ -114,8 +119,23 @@ int32_t fdas_bank_rows(const fdas_params *p);
 /* Size of the template bank in floats: fdas_bank_rows(p) * (L + 16) * 2. */
 int64_t fdas_bank_floats(const fdas_params *p);
 
-/* Number of overlap-save segments for nb bins: ceil(nb / (L - M)). */
+/* Number of overlap-save segments for nb bins at overlap M: ceil(nb / (L - M)). */
 int64_t fdas_num_segments(const fdas_params *p, int64_t nb);
+
+#define FDAS_MAX_GROUPS 4
+
+/* Template groups of the convolver.  Group g covers count[g] plane rows:
+ * the bank rows first_row[g] .. first_row[g+1]-1 and, on a symmetric grid,
+ * their -z partners (z = 0 once, in group 0); its segments discard
+ * overlap[g] points (>= 2 h + 2 for each of its templates, a multiple of 4,
+ * at least 64, at most M), so they yield L - overlap[g] bins each.  The
+ * groups minimise the convolver's work, sum over groups of
+ * (count + 0.5) / (L - overlap) (a segment's forward FFT costs about half
+ * a template pass).  overlap, first_row, count: (host) FDAS_MAX_GROUPS
+ * entries each, or NULL.  Returns the number of groups (1 on grids that are
+ * not symmetric), or FDAS_E_INVAL. */
+int32_t fdas_template_groups(const fdas_params *p, int32_t *overlap, int32_t *first_row,
+                             int32_t *count);
 
 /* Plane row width in floats for nb bins (2*nb with interbinning, else nb). */
 int64_t fdas_plane_width(const fdas_params *p, int64_t nb);

@@ -17,6 +17,7 @@ __all__ = [
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
+    "fdas_template_groups", "FDAS_MAX_GROUPS",
     "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
@@ -39,6 +40,7 @@ FDAS_STATUS_TIMEOUT = 1
 FDAS_STATUS_OVERFLOW = 2
 FDAS_CAND_PEAK = 1
 FDAS_NOALLOC_MAX_N = 1 << 20
+FDAS_MAX_GROUPS = 4
 FDAS_PREC_FP32 = 0
 FDAS_PREC_FP16_SPLIT = 1
 FDAS_PREC_BF16_SPLIT = 2
@@ -99,6 +101,7 @@ def load_library():
         "fdas_num_segments": (c_i64, [P(fdas_params), c_i64]),
         "fdas_bank_floats": (c_i64, [P(fdas_params)]),
         "fdas_plane_width": (c_i64, [P(fdas_params), c_i64]),
+        "fdas_template_groups": (c_i32, [P(fdas_params), c_vp, c_vp, c_vp]),
         "fdas_make_templates": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
         "fdas_normalise_workspace_bytes": (c_sz, [c_i64]),
         "fdas_normalise": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]),
@@ -199,6 +202,16 @@ def fdas_num_segments(p: fdas_params, nb: int) -> int:
 
 def fdas_plane_width(p: fdas_params, nb: int) -> int:
     return _check(load_library().fdas_plane_width(ctypes.byref(p), int(nb)), "fdas_plane_width")
+
+
+def fdas_template_groups(p: fdas_params):
+    """[(overlap, first bank row, plane rows), ...] of the convolver's template groups."""
+    ov = (c_i32 * FDAS_MAX_GROUPS)()
+    fr = (c_i32 * FDAS_MAX_GROUPS)()
+    ct = (c_i32 * FDAS_MAX_GROUPS)()
+    n = _check(load_library().fdas_template_groups(ctypes.byref(p), ov, fr, ct),
+               "fdas_template_groups")
+    return [(ov[k], fr[k], ct[k]) for k in range(n)]
 
 
 def fdas_make_templates(p: fdas_params, bank, stream=None) -> None:

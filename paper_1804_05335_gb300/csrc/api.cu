@@ -10,6 +10,77 @@ static int32_t half_width_i(int32_t z) {
     return (az + 1) / 2 + 8;   // ceil(|z|/2) + 8
 }
 
+// Splits a symmetric grid's bank rows (z >= 0, |z| increasing) into at most
+// kMaxGroups runs of consecutive rows.  A template of half-width h needs an
+// overlap of at least 2h + 2 points (h on each side plus the half bin's
+// neighbour), rounded up to a multiple of 4 and at least 64; a group uses the
+// overlap of its last (widest) row.  The split minimises the convolver's
+// work, sum over groups of (rows + kSegmentFft) / (L - overlap): a group's
+// segments each cost one forward FFT plus one pass per template, and the
+// forward FFT (no template product, no powers) costs about half a pass.  Dynamic programming over the runs of rows that
+// need the same overlap.
+// The overlap only moves the segment boundaries: the correlation values are
+// the same for every overlap that fits the template.  Other grids: one group
+// with overlap M.
+constexpr double kSegmentFft = 0.5;
+
+static void plan_groups(const fdas_params* p, Grid* g) {
+    g->ng = 1;
+    g->gM[0] = p->M;
+    g->gb0[0] = 0;
+    g->gK[0] = g->K;
+    if (!g->sym) return;
+    // runs of equal overlap: run r = bank rows [rs[r], rs[r+1]) with overlap rm[r]
+    // (overlaps are multiples of 4 in [64, L/2]: at most 497 runs)
+    constexpr int kRuns = 512;
+    int rs[kRuns + 1], rm[kRuns], nr = 0;
+    for (int b = 0; b < g->Kb; ++b) {
+        const int z = p->zmin + (g->j0 + b) * p->zstep;
+        int m = ((2 * half_width_i(z) + 2 + 3) / 4) * 4;
+        if (m < 64) m = 64;
+        if (nr > 0 && rm[nr - 1] == m) continue;
+        if (nr == kRuns) return;   // cannot happen for overlaps <= L/2; keep one group
+        rs[nr] = b;
+        rm[nr] = m;
+        ++nr;
+    }
+    rs[nr] = g->Kb;
+    auto rows = [&](int r0, int r1) {
+        return 2 * (rs[r1] - rs[r0]) - ((g->zero && rs[r0] == 0) ? 1 : 0);
+    };
+    // best[k][r]: runs [0, r) in k groups
+    double best[kMaxGroups + 1][kRuns + 1];
+    int from[kMaxGroups + 1][kRuns + 1];
+    for (int k = 0; k <= kMaxGroups; ++k)
+        for (int r = 0; r <= nr; ++r) best[k][r] = 1e300;
+    best[0][0] = 0.0;
+    for (int k = 1; k <= kMaxGroups; ++k)
+        for (int r1 = 1; r1 <= nr; ++r1)
+            for (int r0 = 0; r0 < r1; ++r0) {
+                if (best[k - 1][r0] >= 1e300) continue;
+                const double c = best[k - 1][r0] +
+                                 ((double)rows(r0, r1) + kSegmentFft) / (double)(p->L - rm[r1 - 1]);
+                if (c < best[k][r1]) {
+                    best[k][r1] = c;
+                    from[k][r1] = r0;
+                }
+            }
+    int kb = 1;
+    for (int k = 2; k <= kMaxGroups; ++k)
+        if (best[k][nr] < best[kb][nr] * (1.0 - 1e-9)) kb = k;
+    int ends[kMaxGroups + 1];
+    for (int k = kb, r = nr; k >= 0; --k) {
+        ends[k] = r;
+        if (k > 0) r = from[k][r];
+    }
+    g->ng = kb;
+    for (int k = 0; k < kb; ++k) {
+        g->gb0[k] = rs[ends[k]];
+        g->gK[k] = rows(ends[k], ends[k + 1]);
+        g->gM[k] = rm[ends[k + 1] - 1];
+    }
+}
+
 int make_grid(const fdas_params* p, Grid* g) {
     if (!p || !g) return FDAS_E_INVAL;
     if (p->L != 1024 && p->L != 2048 && p->L != 4096) return FDAS_E_INVAL;
@@ -35,7 +106,17 @@ int make_grid(const fdas_params* p, Grid* g) {
         g->Kb = g->K;
         g->zero = 0;
     }
+    plan_groups(p, g);
     return FDAS_OK;
+}
+
+int64_t series_items(const Grid& g, int L, int64_t nb) {
+    int64_t items = 0;
+    for (int k = 0; k < g.ng; ++k) {
+        const int64_t B = L - g.gM[k];
+        items += ((nb + B - 1) / B) * g.gK[k];
+    }
+    return items;
 }
 
 }  // namespace fdas
@@ -83,6 +164,19 @@ int64_t fdas_num_segments(const fdas_params* p, int64_t nb) {
     if (make_grid(p, &g) != FDAS_OK || nb < 1) return FDAS_E_INVAL;
     int64_t B = p->L - p->M;
     return (nb + B - 1) / B;
+}
+
+int32_t fdas_template_groups(const fdas_params* p, int32_t* overlap, int32_t* first_row,
+                             int32_t* count) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    for (int k = 0; k < g.ng; ++k) {
+        if (overlap) overlap[k] = g.gM[k];
+        if (first_row) first_row[k] = g.gb0[k];
+        if (count) count[k] = g.gK[k];
+    }
+    return g.ng;
 }
 
 int64_t fdas_plane_width(const fdas_params* p, int64_t nb) {
@@ -150,7 +244,6 @@ int64_t fdas_batch_plan(const fdas_params* p, fdas_trial* trials, int32_t ntrial
     int rc = make_grid(p, &g);
     if (rc != FDAS_OK) return rc;
     if (!trials || ntrials < 1) return FDAS_E_INVAL;
-    const int64_t B = p->L - p->M;
     int64_t items = 0;
     for (int32_t i = 0; i < ntrials; ++i) {
         fdas_trial& t = trials[i];
@@ -159,7 +252,7 @@ int64_t fdas_batch_plan(const fdas_params* p, fdas_trial* trials, int32_t ntrial
         const int64_t width = p->interbin ? 2 * t.nb : t.nb;
         if (t.row_stride < width || (t.row_stride % 4) != 0) return FDAS_E_INVAL;
         t.item_begin = items;
-        items += ((t.nb + B - 1) / B) * g.K;
+        items += series_items(g, p->L, t.nb);
     }
     return items;
 }

@@ -63,6 +63,12 @@ struct ConvArgs {
     int32_t* status;
     const fdas_trial* trials;   // batched launches: device table of ntrials series
     int32_t ntrials;
+    // template groups (Grid): overlap, first bank row and template count of
+    // each; a series' items are group-major, segment-major within a group
+    int32_t ng;
+    int32_t gM[kMaxGroups];
+    int32_t gb0[kMaxGroups];
+    int32_t gK[kMaxGroups];
 };
 
 template <int L>
@@ -90,20 +96,29 @@ __device__ __forceinline__ void emit(const ConvArgs& A, int row, int64_t col, fl
     }
 }
 
-// Template of item q inside a segment: bank row, plane row, conjugation.
-// Items of a symmetric grid pair +z with -z so that both use one bank row.
-__device__ __forceinline__ void item_row(const ConvArgs& A, int q, int& row, int& brow, int& cj) {
+// Template q of group g inside a segment: bank row, plane row, conjugation.
+// Items of a symmetric grid pair +z with -z so that both use one bank row;
+// group g holds bank rows gb0[g] onwards (z = 0 first in group 0).
+__device__ __forceinline__ void item_row(const ConvArgs& A, int g, int q, int& row, int& brow,
+                                         int& cj) {
     if (!A.sym) {
         row = q; brow = q; cj = 0;
         return;
     }
-    if (A.zero) {
+    const int b0 = A.gb0[g];
+    if (A.zero && b0 == 0) {
         if (q == 0) { brow = 0; cj = 0; }
         else { brow = (q + 1) >> 1; cj = (q & 1) ? 0 : 1; }
     } else {
-        brow = q >> 1; cj = q & 1;
+        brow = b0 + (q >> 1); cj = q & 1;
     }
     row = cj ? (A.K - 1 - A.j0 - brow) : (A.j0 + brow);
+}
+
+// Segments of a series of nb bins in group g.
+__device__ __forceinline__ int64_t group_segments(const ConvArgs& A, int L, int g, int64_t nb) {
+    const int64_t B = L - A.gM[g];
+    return (nb + B - 1) / B;
 }
 
 // Powers of one pair of positions (j, j+1) given x[j], x[j+1], x[j+2].
@@ -162,7 +177,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 
     const int t = threadIdx.x;
     const int a = t / Q, c = t % Q;
-    const int M = A.M, B = L - M, NP = B / 2;
+    int M = A.M, B = L - M, NP = B / 2;   // of the current item's group
 
     const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
     const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
@@ -179,10 +194,22 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     }
     SeriesState st = series_of<BATCH>(A, trial);
     const int64_t first = BATCH ? A.trials[trial].item_begin : 0;
-    int64_t s = (lo - first) / A.K;
-    int q = (int)(lo - first - s * A.K);
+    // group, segment and template of the first item
+    int grp = 0;
+    int64_t rel = lo - first;
+    int64_t gseg = group_segments(A, L, 0, st.nb);
+    while (rel >= gseg * A.gK[grp] && grp + 1 < A.ng) {
+        rel -= gseg * A.gK[grp];
+        ++grp;
+        gseg = group_segments(A, L, grp, st.nb);
+    }
+    M = A.gM[grp];
+    B = L - M;
+    NP = B / 2;
+    int64_t s = rel / A.gK[grp];
+    int q = (int)(rel - s * A.gK[grp]);
     int row, brow, cj;
-    item_row(A, q, row, brow, cj);
+    item_row(A, grp, q, row, brow, cj);
 
     if (t == 0) {
         mbar_init(&hbar, 1);
@@ -228,7 +255,8 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     const int hstep = (t == 0) ? 1 : T;
     __syncthreads();
 
-    int64_t cur_seg = -1;
+    int64_t cur_seg = -1;   // segment (and group) of the forward FFT held in Y
+    int cur_grp = -1;
     int parity = 0;
     uint32_t hphase = 0;
     bool hpending = true;
@@ -243,12 +271,19 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 st = series_of<BATCH>(A, trial);
                 s = 0;
                 q = 0;
+                grp = 0;
+                gseg = group_segments(A, L, 0, st.nb);
+                M = A.gM[0];
+                B = L - M;
+                NP = B / 2;
+                item_row(A, 0, 0, row, brow, cj);
                 cur_seg = -1;
             }
         }
-        if (s != cur_seg) {
-            // ---- forward FFT of segment s, once per segment ----
+        if (s != cur_seg || grp != cur_grp) {
+            // ---- forward FFT of segment s, once per segment (and group) ----
             cur_seg = s;
+            cur_grp = grp;
             const int64_t base = s * (int64_t)B - M / 2;
             if constexpr (PREC == 0) {
 #pragma unroll
@@ -342,11 +377,20 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         }
 
         // ---- next item; prefetch its template row if it changes ----
-        const int64_t s_next = (q + 1 == A.K) ? s + 1 : s;
-        const int q_next = (q + 1 == A.K) ? 0 : q + 1;
+        int64_t s_next = s;
+        int q_next = q + 1, grp_next = grp;
+        if (q_next == A.gK[grp]) {
+            q_next = 0;
+            if (++s_next == gseg) {
+                s_next = 0;
+                // the series is done after its last group; a batched launch
+                // continues with the next series' first group
+                if (++grp_next == A.ng) grp_next = 0;
+            }
+        }
         int row_n = 0, brow_n = brow, cj_n = 0;
         if (w + 1 < hi) {
-            item_row(A, q_next, row_n, brow_n, cj_n);
+            item_row(A, grp_next, q_next, row_n, brow_n, cj_n);
             if (brow_n != brow) {
                 if (t == 0) {
                     fence_proxy_async();
@@ -458,6 +502,13 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         parity ^= 1;
         s = s_next;
         q = q_next;
+        if (grp_next != grp) {
+            grp = grp_next;
+            gseg = group_segments(A, L, grp, st.nb);
+            M = A.gM[grp];
+            B = L - M;
+            NP = B / 2;
+        }
         row = row_n;
         brow = brow_n;
         cj = cj_n;
@@ -502,6 +553,12 @@ inline ConvArgs base_args(const fdas_params* p, const Grid& g, const float4* ban
     a.items = 0;
     a.bank = bank;
     a.K = g.K;
+    a.ng = g.ng;
+    for (int k = 0; k < kMaxGroups; ++k) {
+        a.gM[k] = k < g.ng ? g.gM[k] : p->M;
+        a.gb0[k] = k < g.ng ? g.gb0[k] : 0;
+        a.gK[k] = k < g.ng ? g.gK[k] : 1;
+    }
     a.j0 = g.j0;
     a.sym = g.sym;
     a.zero = g.zero;

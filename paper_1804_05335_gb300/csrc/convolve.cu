@@ -30,8 +30,7 @@ int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, in
     a.nb = nb;
     a.plane = plane;
     a.row_stride = row_stride;
-    const int64_t B = p->L - p->M;
-    a.items = ((nb + B - 1) / B) * g.K;
+    a.items = series_items(g, p->L, nb);
     if (fused) {
         cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return FDAS_E_CUDA;

@@ -42,7 +42,6 @@ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
 // tw[q] = exp(-i 2 pi q / R), q < R.  Ends with a barrier; returns x.
 template <int R1>
 __device__ void tile_dft_r(float2* x, float2* y, const float2* tw) {
-    constexpr int R = 16 * R1;
     const int t = threadIdx.x, col = t & 15, jj = t >> 4;
     float2 v[16];
     if constexpr (R1 > 1) {

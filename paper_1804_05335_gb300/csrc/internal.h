@@ -7,6 +7,8 @@
 
 namespace fdas {
 
+constexpr int kMaxGroups = FDAS_MAX_GROUPS;
+
 // Template grid and bank-row bookkeeping derived from fdas_params.
 struct Grid {
     int32_t K;       // templates (plane rows)
@@ -15,10 +17,20 @@ struct Grid {
     int32_t sym;     // 1: symmetric grid, bank holds z >= 0 only
     int32_t zero;    // 1: z = 0 is on a symmetric grid
     int32_t hmax;    // largest half-width on the grid
+    // Template groups of increasing |z| (symmetric grids; one group otherwise),
+    // each convolved with the smallest overlap its longest template needs.
+    int32_t ng;
+    int32_t gM[kMaxGroups];    // overlap (discarded points per segment) of group g
+    int32_t gb0[kMaxGroups];   // first bank row of group g
+    int32_t gK[kMaxGroups];    // templates (plane rows) of group g
 };
 
-// Validates p; returns FDAS_OK and fills g, or FDAS_E_INVAL.
+// Validates p; returns FDAS_OK and fills g (groups included), or FDAS_E_INVAL.
 int make_grid(const fdas_params* p, Grid* g);
+
+// Work items (segment, template) of one series of nb bins: for each group,
+// ceil(nb / (L - gM)) segments times gK templates.
+int64_t series_items(const Grid& g, int L, int64_t nb);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_E_CUDA; }
 

@@ -104,3 +104,47 @@ def _slot(k, L):
 def test_bank_layout_is_a_permutation(L):
     s = np.array([_slot(k, L) for k in range(L)])
     assert sorted(s) == list(range(L))
+
+
+def _needed_overlap(z):
+    """Overlap a template needs, as fdas.h states it: >= 2h + 2, multiple of 4, >= 64."""
+    h = F.fdas_half_width(z)
+    return max(64, -(-(2 * h + 2) // 4) * 4)
+
+
+@pytest.mark.parametrize("L,M,zmax,zstep", [(2048, 256, 200, 2), (2048, 128, 58, 2),
+                                            (1024, 64, 20, 2), (4096, 256, 201, 3)])
+def test_template_groups_cover_the_grid_and_minimise_work(L, M, zmax, zstep):
+    import itertools
+    p = F.params(L, M, -zmax, zmax, zstep, 1)
+    groups = F.fdas_template_groups(p)
+    K, Kb = F.fdas_num_templates(p), F.fdas_bank_rows(p)
+    j0 = K - Kb
+    zb = [-zmax + (j0 + b) * zstep for b in range(Kb)]
+    zero = zb[0] == 0
+    assert 1 <= len(groups) <= F.FDAS_MAX_GROUPS
+    assert sum(c for _, _, c in groups) == K
+    firsts = [f for _, f, _ in groups] + [Kb]
+    assert firsts[0] == 0 and all(a < b for a, b in zip(firsts, firsts[1:]))
+
+    def rows(lo, hi):
+        return 2 * (hi - lo) - (1 if zero and lo == 0 else 0)
+
+    for k, (ov, f, c) in enumerate(groups):
+        assert c == rows(f, firsts[k + 1])
+        assert ov == max(_needed_overlap(z) for z in zb[f:firsts[k + 1]]) and ov <= M
+    work = sum((c + 0.5) / (L - ov) for ov, _, c in groups)
+    # brute force over every split of the bank rows into at most 4 runs
+    best = float("inf")
+    for n in range(1, F.FDAS_MAX_GROUPS + 1):
+        for cut in itertools.combinations(range(1, Kb), n - 1):
+            ends = (0,) + cut + (Kb,)
+            w = sum((rows(a, b) + 0.5) / (L - _needed_overlap(zb[b - 1]))
+                    for a, b in zip(ends, ends[1:]))
+            best = min(best, w)
+    assert work <= best * (1 + 1e-12)
+
+
+def test_template_groups_one_group_off_symmetric_grids():
+    p = F.params(2048, 128, -10, 30, 5, 1)
+    assert F.fdas_template_groups(p) == [(128, 0, F.fdas_num_templates(p))]
