@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched / refinement / split-precision measurements")
     ap.add_argument("--batch-trials", type=int, default=256)
+    ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2],
+                    help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo")
     return ap.parse_args()
 
 
@@ -64,6 +66,29 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def fp32_roofline(S, kernel_ms, sm_mhz, sms):
+    """Secondary roofline of the convolver: algorithmic FP32 flops per launch
+    (textbook radix-2 counts: 5 L log2 L per L-point FFT, 6 per complex
+    product, 3 per full-bin and 6 per half-bin power) over the launch time,
+    against SMs x 128 FP32 lanes x 2 flops x the sampled SM clock."""
+    import math
+    from paper_1804_05335_gb300 import fdas_template_groups
+    L, nb = S.L, S.nb
+    fft = 5.0 * L * math.log2(L)
+    flops = 0.0
+    for ov, _, count in fdas_template_groups(S.p):
+        B = L - ov
+        nseg = -(-nb // B)
+        flops += nseg * fft                                   # segment FFT per group
+        flops += nseg * count * (fft + 6.0 * L + 9.0 * B)     # product, inverse FFT, powers
+    peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (kernel_ms / 1e3) / 1e12
+    return {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_launch": flops,
+            "flops_per_point": flops / (S.K * S.width),
+            "peak_source": "%d SMs x 128 lanes x 2 flop x %.0f MHz (sampled)" % (sms, sm_mhz)}
 
 
 def rank_seed(seed, rank):
@@ -403,6 +428,7 @@ def run_native(args):
     x = synth.make_series(wl.n, wl.injections, rank_seed(wl.seed, rank))
     S = Search(wl.n, wl.L, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
                median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
+    S.prec = args.prec
     host_series = torch.from_numpy(x).pin_memory()
     S.series.copy_(host_series)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -434,7 +460,7 @@ def run_native(args):
         ea.record()
         S.normalise()
         e1.record()
-        S.correlate(True)
+        S.correlate(True, prec=args.prec)
         e2.record()
     torch.cuda.synchronize()
     barrier()
@@ -467,11 +493,13 @@ def run_native(args):
         conv_mean = statistics.mean(conv_ms)
         alg_bytes = S.K * S.width * 4 + S.nb * 8 + S.Kb * S.L * 8
         achieved = alg_bytes / (conv_mean / 1e3) / 1e9
-        key = "conv_kernel<%d,true>" % wl.L
+        key = "conv_kernel<%d,true>" % wl.L + ("" if args.prec == 0 else "/prec%d" % args.prec)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "f16x2-split+f32", 2: "bf16x2-split+f32"}[args.prec],
+            "data": "synthetic",
             "config": {"workload": describe(wl), "n": wl.n, "nb": wl.nb, "K": S.K, "L": wl.L,
                        "M": wl.M, "segments": S.nseg, "plane_points": points,
                        "plane_bytes": points * 4, "per_rank": "independent series per rank",
@@ -483,6 +511,9 @@ def run_native(args):
                          if peak_kind == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel_ms": conv_mean},
+            "roofline_fp32": fp32_roofline(
+                S, conv_mean, clocks.get("sm_mhz") or 2070.0,
+                torch.cuda.get_device_properties(dev).multi_processor_count),
             "front_ms": statistics.mean(a - b for a, b in zip(step_ms, conv_ms)),
             "templates_ms": statistics.mean(tpl_ms),
             "e2e": {"value": e2e_value, "unit": UNIT,

@@ -47,6 +47,7 @@ class Search:
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.fused = fdas_fused_threshold(self.thr, int(self.cand.data_ptr()), self.cap,
                                           int(self.count.data_ptr()))
+        self.prec = 0   # DFT arithmetic of step() and stream() (FDAS_PREC_*)
 
     # ---- the calls ----
     def make_templates(self, stream=None):
@@ -75,7 +76,7 @@ class Search:
         """One pass of the hot path: bank, spectrum, plane + fused candidates."""
         self.make_templates(stream)
         self.normalise(stream, series)
-        self.correlate(True, stream=stream)
+        self.correlate(True, stream=stream, prec=self.prec)
 
     def stream(self, host_series, host_out):
         """Search the pinned host series host_series[i] (n float32 each) one
@@ -106,7 +107,7 @@ class Search:
             self.normalise(series=self._inbuf[j])
             free[j] = torch.cuda.Event()
             free[j].record(main)
-            self.correlate(True)
+            self.correlate(True, prec=self.prec)
             host_out[i][:1].copy_(self.count, non_blocking=True)
             host_out[i][1:].copy_(self.cand, non_blocking=True)
 

@@ -213,12 +213,15 @@ def test_production_plane_sampled(F, L):
     torch.cuda.synchronize()
     plane = S.plane2d()
     zs = O.z_grid(wl.zmin, wl.zmax, wl.zstep)
+    # every row over 64 random 4096-column windows, both ends and every
+    # injection's neighbourhood
     rng = np.random.default_rng(L)
-    starts = list(rng.integers(0, wl.nb - 256, 8)) + [0, wl.nb - 256]
-    starts += [int(r0) - 128 for r0, _, _ in wl.injections]
-    for r0 in starts:
-        got = plane[:, 2 * r0: 2 * (r0 + 256)].cpu().numpy().astype(np.float64)
-        ref = O.plane_window(A64, zs, r0, 256)
+    wins = [(int(r), 2048) for r in rng.integers(0, wl.nb - 2048, 64)]
+    wins += [(0, 2048), (wl.nb - 2048, 2048)]
+    wins += [(int(r0) - 128, 256) for r0, _, _ in wl.injections]
+    for r0, w in wins:
+        got = plane[:, 2 * r0: 2 * (r0 + w)].cpu().numpy().astype(np.float64)
+        ref = O.plane_window(A64, zs, r0, w)
         assert np.abs(got - ref).max() < PTOL, (r0, np.abs(got - ref).max())
     # every fused candidate is a true crossing (oracle value within tolerance)
     r, c, p, fl, total = S.candidates()
