@@ -317,6 +317,46 @@ def batched_row(args, torch, dev):
                       % (ntr, len(bs.waves))}
 
 
+def plane16_row(args, torch, dev, S, wl):
+    """The production plane written as 16-bit floats (2 bytes per point):
+    convolver time and bandwidth against the FP32 plane, and the fused
+    candidate list (must equal the FP32 call's)."""
+    from paper_1804_05335_gb300 import FDAS_PLANE_BF16, FDAS_PLANE_F16, fdas_correlate_plane16
+    peak, _ = measured_peak()
+    S.correlate(fused=True)
+    rf, cf, pf, _, _ = S.candidates()
+    buf = torch.empty(S.K * S.row_stride, dtype=torch.float16, device=dev)
+    out = {}
+    reps = 10
+    for name, ptype in (("f32", 0), ("f16", FDAS_PLANE_F16), ("bf16", FDAS_PLANE_BF16)):
+        def run():
+            if ptype == 0:
+                S.correlate(fused=True)
+            else:
+                fdas_correlate_plane16(S.p, ptype, S.spec, S.nb, S.bank, buf, S.row_stride,
+                                       S.fused, S.status)
+        for _ in range(3):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r, c, pw, _, tot = S.candidates()
+        esize = 4 if ptype == 0 else 2
+        alg = S.K * S.width * esize + S.nb * 8 + S.Kb * S.L * 8
+        out[name] = {"conv_ms": ms, "plane_bytes": S.K * S.width * esize,
+                     "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                     "frac_of_peak": alg / (ms / 1e3) / 1e9 / peak,
+                     "points_per_s": S.K * S.width / (ms / 1e3),
+                     "candidates_equal_fp32": bool(np.array_equal(r, rf) and np.array_equal(c, cf)
+                                                   and np.array_equal(pw, pf))}
+    del buf
+    return {"workload": "production plane, L=%d" % S.L, "reps": reps, "planes": out}
+
+
 def split_row(args, torch, dev, S, wl):
     """The production plane with the four radix-16 DFT passes of every segment
     FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
@@ -524,6 +564,7 @@ def run_native(args):
         }
         if ws == 1 and not args.no_rows:
             line["rows"] = {"a9_split": split_row(args, torch, dev, S, wl)}
+            line["rows"]["f1_plane16"] = plane16_row(args, torch, dev, S, wl)
             line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()

@@ -237,6 +237,28 @@ int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const fl
                    float *plane, int64_t row_stride, const fdas_fused_threshold *fused,
                    int32_t *status, void *stream);
 
+/* 16-bit plane element types (fdas_correlate_plane16). */
+#define FDAS_PLANE_F16 1        /* IEEE binary16: 11 significant bits, largest finite 65504 */
+#define FDAS_PLANE_BF16 2       /* bfloat16: 8 significant bits, FP32 range */
+
+/*
+ * fdas_correlate_plane16 -- fdas_correlate writing the plane as 16-bit
+ * floats, 2 bytes per point instead of 4 (half the plane's memory and write
+ * traffic; e.g. for harmonic summing or for more dispersion trials per plane
+ * pool).  Powers are computed in FP32 exactly as in fdas_correlate and
+ * rounded to nearest on the store; a power above 65504 becomes +inf in FP16.
+ * The fused threshold compares the FP32 values, so its candidates, with their
+ * FP32 powers, equal those of fdas_correlate.
+ * type: FDAS_PLANE_F16 or FDAS_PLANE_BF16.
+ * plane: (device) K rows of row_stride 16-bit elements, 16-byte aligned;
+ *   row_stride >= fdas_plane_width and a multiple of 4.
+ * Other arguments, layout and errors as fdas_correlate; FDAS_E_INVAL for any
+ * other type.
+ */
+int fdas_correlate_plane16(const fdas_params *p, int32_t type, const float *spec, int64_t nb,
+                           const float *bank, void *plane, int64_t row_stride,
+                           const fdas_fused_threshold *fused, int32_t *status, void *stream);
+
 /* Arithmetic of the convolver's radix-16 DFT passes (fdas_correlate_split). */
 #define FDAS_PREC_FP32 0        /* FP32 on the CUDA cores, as fdas_correlate */
 #define FDAS_PREC_FP16_SPLIT 1  /* FP16 hi+lo operands on tensor cores, FP32 accumulation */

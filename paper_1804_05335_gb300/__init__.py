@@ -18,6 +18,7 @@ __all__ = [
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
+    "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16",
     "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
@@ -41,6 +42,8 @@ FDAS_STATUS_OVERFLOW = 2
 FDAS_CAND_PEAK = 1
 FDAS_NOALLOC_MAX_N = 1 << 20
 FDAS_MAX_GROUPS = 4
+FDAS_PLANE_F16 = 1
+FDAS_PLANE_BF16 = 2
 FDAS_PREC_FP32 = 0
 FDAS_PREC_FP16_SPLIT = 1
 FDAS_PREC_BF16_SPLIT = 2
@@ -110,6 +113,8 @@ def load_library():
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_correlate_split": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
                                                 c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
+        "fdas_correlate_plane16": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
+                                                  c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
         "fdas_batch_plan": (c_i64, [P(fdas_params), P(fdas_trial), c_i32]),
@@ -250,6 +255,16 @@ def fdas_correlate(p: fdas_params, spec, nb: int, bank, plane, row_stride: int,
     _check(load_library().fdas_correlate(ctypes.byref(p), _ptr(spec), int(nb), _ptr(bank),
                                          _ptr(plane), int(row_stride), f, _ptr(status),
                                          _stream(stream)), "fdas_correlate")
+
+
+def fdas_correlate_plane16(p: fdas_params, ptype: int, spec, nb: int, bank, plane, row_stride: int,
+                           fused: fdas_fused_threshold | None = None, status=None,
+                           stream=None) -> None:
+    f = ctypes.byref(fused) if fused is not None else None
+    _check(load_library().fdas_correlate_plane16(ctypes.byref(p), int(ptype), _ptr(spec),
+                                                 int(nb), _ptr(bank), _ptr(plane),
+                                                 int(row_stride), f, _ptr(status),
+                                                 _stream(stream)), "fdas_correlate_plane16")
 
 
 def fdas_correlate_split(p: fdas_params, prec: int, spec, nb: int, bank, plane, row_stride: int,

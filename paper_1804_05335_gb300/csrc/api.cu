@@ -222,6 +222,19 @@ int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const fl
                             status, (cudaStream_t)stream);
 }
 
+int fdas_correlate_plane16(const fdas_params* p, int32_t type, const float* spec, int64_t nb,
+                           const float* bank, void* plane, int64_t row_stride,
+                           const fdas_fused_threshold* fused, int32_t* status, void* stream) {
+    if (type != FDAS_PLANE_F16 && type != FDAS_PLANE_BF16) return FDAS_E_INVAL;
+    Grid g;
+    int rc = check_correlate(p, &g, spec, nb, bank, static_cast<const float*>(plane), row_stride,
+                             fused, status);
+    if (rc != FDAS_OK) return rc;
+    return launch_correlate_plane16(p, g, type, reinterpret_cast<const float2*>(spec), nb,
+                                    reinterpret_cast<const float4*>(bank), plane, row_stride,
+                                    fused, status, (cudaStream_t)stream);
+}
+
 int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, int64_t nb,
                          const float* bank, float* plane, int64_t row_stride,
                          const fdas_fused_threshold* fused, int32_t* status, void* stream) {

@@ -36,6 +36,9 @@
 #pragma once
 #include <algorithm>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "conv_fft.cuh"
 #include "internal.h"
 #include "split_mma.cuh"
@@ -121,6 +124,53 @@ __device__ __forceinline__ int64_t group_segments(const ConvArgs& A, int L, int 
     return (nb + B - 1) / B;
 }
 
+// Plane stores by element type OUT (0 float, 1 IEEE half, 2 bfloat16; values
+// rounded to nearest): 4, 2 or 1 consecutive elements from element i of a row.
+// The 4- and 2-element stores are streaming and need 4-element alignment
+// (16 bytes for float, 8 for the 16-bit types) and 2-element alignment.
+template <int OUT>
+__device__ __forceinline__ void plane_store4(void* row, int64_t i, float4 v) {
+    if constexpr (OUT == 0) {
+        __stcs(reinterpret_cast<float4*>(static_cast<float*>(row) + i), v);
+    } else {
+        uint2 u;
+        if constexpr (OUT == 1) {
+            __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+            u = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+        } else {
+            __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+            u = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+        }
+        __stcs(reinterpret_cast<uint2*>(static_cast<uint16_t*>(row) + i), u);
+    }
+}
+template <int OUT>
+__device__ __forceinline__ void plane_store2(void* row, int64_t i, float2 v) {
+    if constexpr (OUT == 0) {
+        __stcs(reinterpret_cast<float2*>(static_cast<float*>(row) + i), v);
+    } else {
+        uint32_t u;
+        if constexpr (OUT == 1) {
+            __half2 a = __floats2half2_rn(v.x, v.y);
+            u = *reinterpret_cast<uint32_t*>(&a);
+        } else {
+            __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+            u = *reinterpret_cast<uint32_t*>(&a);
+        }
+        __stcs(reinterpret_cast<unsigned int*>(static_cast<uint16_t*>(row) + i), u);
+    }
+}
+template <int OUT>
+__device__ __forceinline__ void plane_store1(void* row, int64_t i, float v) {
+    if constexpr (OUT == 0) {
+        static_cast<float*>(row)[i] = v;
+    } else if constexpr (OUT == 1) {
+        reinterpret_cast<__half*>(row)[i] = __float2half_rn(v);
+    } else {
+        reinterpret_cast<__nv_bfloat16*>(row)[i] = __float2bfloat16_rn(v);
+    }
+}
+
 // Powers of one pair of positions (j, j+1) given x[j], x[j+1], x[j+2].
 __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
     const float hs = 0.61685027506808491f;   // (pi/4)^2
@@ -163,7 +213,7 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
     return st;
 }
 
-template <int L, bool FUSE, bool BATCH, int PREC>
+template <int L, bool FUSE, bool BATCH, int PREC, int OUT>
 __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const ConvArgs A) {
     using S = ConvShape<L>;
     constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
@@ -425,32 +475,33 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 
         // ---- epilogue: powers of positions M/2 .. M/2+B, two bins per pair ----
         const int64_t r0 = s * (int64_t)B;
-        float* prow = st.plane + (int64_t)row * st.row_stride;
+        // plane row (elements of type OUT)
+        void* prow = OUT == 0 ? static_cast<void*>(st.plane + (int64_t)row * st.row_stride)
+                              : static_cast<void*>(reinterpret_cast<uint16_t*>(st.plane) +
+                                                   (int64_t)row * st.row_stride);
         const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
         const float2* o2 = outb + M / 2 + 2;
         float mx = 0.f;
         if (r0 + B < st.nb) {
             constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
             if (A.interbin) {
-                float4* dst = reinterpret_cast<float4*>(prow + 2 * r0);
 #pragma unroll
                 for (int u = 0; u < UMAX; ++u) {
                     const int p = t + u * T;
                     if (p < NP) {
                         const float4 pw = pair_powers(o4[p], o2[2 * p]);
-                        __stcs(dst + p, pw);
+                        plane_store4<OUT>(prow, 2 * r0 + 4 * p, pw);
                         if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
                     }
                 }
             } else {
-                float2* dst = reinterpret_cast<float2*>(prow + r0);
 #pragma unroll
                 for (int u = 0; u < UMAX; ++u) {
                     const int p = t + u * T;
                     if (p < NP) {
                         const float4 x = o4[p];
                         const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
-                        __stcs(dst + p, pw);
+                        plane_store2<OUT>(prow, r0 + 2 * p, pw);
                         if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
                     }
                 }
@@ -465,12 +516,15 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 if (r >= st.nb - 1) pw.y = 0.f;           // no bin r+1
                 if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
                 if (A.interbin) {
-                    prow[2 * r] = pw.x;
-                    prow[2 * r + 1] = pw.y;
-                    if (r + 1 < st.nb) { prow[2 * r + 2] = pw.z; prow[2 * r + 3] = pw.w; }
+                    plane_store1<OUT>(prow, 2 * r, pw.x);
+                    plane_store1<OUT>(prow, 2 * r + 1, pw.y);
+                    if (r + 1 < st.nb) {
+                        plane_store1<OUT>(prow, 2 * r + 2, pw.z);
+                        plane_store1<OUT>(prow, 2 * r + 3, pw.w);
+                    }
                 } else {
-                    prow[r] = pw.x;
-                    if (r + 1 < st.nb) prow[r + 1] = pw.z;
+                    plane_store1<OUT>(prow, r, pw.x);
+                    if (r + 1 < st.nb) plane_store1<OUT>(prow, r + 1, pw.z);
                     pw.y = 0.f;
                     pw.w = 0.f;
                 }
@@ -515,13 +569,13 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     }
 }
 
-template <int L, bool FUSE, bool BATCH, int PREC = 0>
+template <int L, bool FUSE, bool BATCH, int PREC = 0, int OUT = 0>
 static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     using S = ConvShape<L>;
     constexpr size_t smem = ConvSmem<L>::bytes;
     static int sms = 0, max_per_sm = 0;
     if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH, PREC>,
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH, PREC, OUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return FDAS_E_CUDA;
@@ -529,7 +583,7 @@ static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
         if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH, PREC>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH, PREC, OUT>,
                                                           S::T, smem) != cudaSuccess)
             return FDAS_E_CUDA;
         if (per_sm < 1) return FDAS_E_UNSUPPORTED;
@@ -538,7 +592,7 @@ static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     }
     const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
     const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
-    conv_kernel<L, FUSE, BATCH, PREC><<<(unsigned)g, S::T, smem, st>>>(args);
+    conv_kernel<L, FUSE, BATCH, PREC, OUT><<<(unsigned)g, S::T, smem, st>>>(args);
     return cuda_status(cudaGetLastError());
 }
 

@@ -45,6 +45,9 @@ int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_tri
                              int32_t ntrials, int64_t total_items, const float4* bank,
                              const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
                              cudaStream_t st);
+int launch_correlate_plane16(const fdas_params* p, const Grid& g, int type, const float2* spec,
+                             int64_t nb, const float4* bank, void* plane, int64_t row_stride,
+                             const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st);
 int launch_correlate_split(const fdas_params* p, const Grid& g, int prec, const float2* spec,
                            int64_t nb, const float4* bank, float* plane, int64_t row_stride,
                            const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st);

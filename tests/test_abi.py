@@ -84,6 +84,11 @@ def test_invalid_buffers_rejected_before_launch():
         lambda: F.fdas_correlate_split(p, 2, 256, 1000, 256, 256, 2002, stream=0),    # stride % 4
         lambda: F.fdas_correlate_split(F.params(L=512), 1, 256, 1000, 256, 256, 2000,
                                        stream=0),                                     # L
+        lambda: F.fdas_correlate_plane16(p, 0, 256, 1000, 256, 256, 2000, stream=0),  # type
+        lambda: F.fdas_correlate_plane16(p, 3, 256, 1000, 256, 256, 2000, stream=0),  # type
+        lambda: F.fdas_correlate_plane16(p, 1, 256, 1000, 256, 0, 2000, stream=0),    # NULL plane
+        lambda: F.fdas_correlate_plane16(p, 2, 256, 1000, 256, 264, 2000, stream=0),  # plane align
+        lambda: F.fdas_correlate_plane16(p, 1, 256, 1000, 256, 256, 2002, stream=0),  # stride % 4
     ]
     for f in cases:
         with pytest.raises(F.FdasError) as e:
