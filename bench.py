@@ -357,6 +357,78 @@ def plane16_row(args, torch, dev, S, wl):
     return {"workload": "production plane, L=%d" % S.L, "reps": reps, "planes": out}
 
 
+def interp2_row(args, torch, dev, S, wl):
+    """2-bin Fourier interpolation (interbin = 2) against interbinning.
+    Time: the production spectrum at M = 436 (>= 4 h(200) + 2).  Scalloping:
+    a 2^20-sample series with 30 strong chirps (S/N 300, so that noise moves
+    the powers by well under 1 %) at fractional frequency offsets 0 .. 1/2
+    bin and fdot offsets 0 .. 1 from the grid (z step 2), at |z| near 10 and
+    150; for each, the largest plane power near the chirp with either method
+    as a fraction of the power at the refined (continuous r, z) optimum."""
+    from paper_1804_05335_gb300.refine import refine
+    from paper_1804_05335_gb300.search import Search
+    S2 = Search(wl.n, 2048, 436, wl.zmin, wl.zmax, wl.zstep, interbin=2,
+                median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
+    S2.spec.copy_(S.spec)
+    S2.make_templates()
+    reps = 5
+    S2.correlate(fused=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        S2.correlate(fused=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    points = S2.K * S2.width
+    del S2
+    torch.cuda.empty_cache()
+
+    n = 1 << 20
+    inj = []
+    for zc in (10.0, -150.0):
+        for fr in (0.0, 0.125, 0.25, 0.375, 0.5):
+            for zo in (0.0, 0.5, 1.0):
+                inj.append((15000.0 * (len(inj) + 1) + fr, zc + zo, 300.0))
+    x = synth.make_series(n, tuple(inj), 4242)
+    zs = np.arange(-200, 201, 2)
+    planes = {}
+    for ib, M in ((1, 256), (2, 436)):
+        T = Search(n, 2048, M, -200, 200, 2, interbin=ib, thr=1e30, device=dev)
+        T.series.copy_(torch.from_numpy(x))
+        T.step()
+        torch.cuda.synchronize()
+        planes[ib] = T.plane2d().cpu().numpy()
+        spec = T.spec.clone()
+        del T
+    res = []
+    for r0, z0, _ in inj:
+        k0 = int(np.argmin(np.abs(zs - z0)))
+        ks = slice(max(0, k0 - 2), k0 + 3)
+        cs = slice(2 * int(r0) - 8, 2 * int(r0) + 10)
+        a1, a2 = planes[1][ks, cs], planes[2][ks, cs]
+        k, c = np.unravel_index(np.argmax(a2), a2.shape)
+        _, _, Pr = refine(spec, torch.tensor([(cs.start + c) / 2.0], dtype=torch.float64, device=dev),
+                          torch.tensor([float(zs[ks.start + k])], dtype=torch.float64, device=dev),
+                          zmax=200, steps=60)
+        Pr = float(Pr.item())
+        res.append((round(r0 % 1.0, 3), round(z0 - zs[k0] if abs(z0 - zs[k0]) <= 1 else z0, 2),
+                    z0, float(a1.max()) / Pr, float(a2.max()) / Pr))
+    f1 = np.array([x[3] for x in res])
+    f2 = np.array([x[4] for x in res])
+    byfrac = {}
+    for fr in (0.0, 0.125, 0.25, 0.375, 0.5):
+        sel = [i for i, x in enumerate(res) if abs(x[0] - fr) < 1e-6]
+        byfrac[str(fr)] = {"interbin": float(f1[sel].mean()), "interp2": float(f2[sel].mean())}
+    return {"time": {"L": 2048, "M": 436, "conv_ms": ms, "points_per_s": points / (ms / 1e3)},
+            "scalloping": {"chirps": len(res), "snr": 300, "series": n,
+                           "power_frac_of_refined": {"interbin_mean": float(f1.mean()),
+                                                     "interbin_min": float(f1.min()),
+                                                     "interp2_mean": float(f2.mean()),
+                                                     "interp2_min": float(f2.min())},
+                           "mean_by_frequency_offset": byfrac}}
+
+
 def split_row(args, torch, dev, S, wl):
     """The production plane with the four radix-16 DFT passes of every segment
     FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
@@ -565,6 +637,7 @@ def run_native(args):
         if ws == 1 and not args.no_rows:
             line["rows"] = {"a9_split": split_row(args, torch, dev, S, wl)}
             line["rows"]["f1_plane16"] = plane16_row(args, torch, dev, S, wl)
+            line["rows"]["f2_interp2"] = interp2_row(args, torch, dev, S, wl)
             line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()

@@ -68,7 +68,15 @@ extern "C" {
  *           index (Section 4.2).
  *  interbin 1: plane rows hold 2*nb columns, column 2r = |F_r|^2 and
  *           column 2r+1 = (pi/4)^2 |F_r - F_{r+1}|^2 (Eq. f-interp), the last
- *           one 0;  0: rows hold nb columns |F_r|^2.
+ *           one 0;  0: rows hold nb columns |F_r|^2;  2: 2-bin Fourier
+ *           interpolation (Section 3, after Eq. f-interp): rows hold 2*nb
+ *           columns, column m = |F(m/2)|^2 with the correlation evaluated at
+ *           every half bin, F(rho) = sum over bins k with |k - rho| <= h of
+ *           spec[k] conj(R_z(k - rho)); the convolver works on the spectrum
+ *           with zeros interleaved (2*nb positions) and templates sampled
+ *           every half bin, so it needs 4h(max|z|) + 2 <= M, and the bank
+ *           holds every template (no +-z pairing: R_{-z}(d) = -conj(R_z(d))
+ *           at half-integer d).
  * The template half-width is h(z) = ceil(|z|/2) + 8 taps. */
 typedef struct {
     int32_t L;

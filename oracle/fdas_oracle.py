@@ -58,6 +58,7 @@ __all__ = [
     "real_spectrum", "normalise", "block_medians", "correlate", "correlate_points",
     "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
     "search", "oracle_threads", "PEAK_FLAG", "response_derivs_quadrature", "refine_taps",
+    "correlate_half", "plane_interp2",
     "refine_power", "refine_grad_spec", "refine_ascent",
 ]
 
@@ -320,6 +321,39 @@ def plane_window(A, zs, r0: int, nr: int, interbin: bool = True) -> np.ndarray:
     extra = 0 if ends else 1
     F = correlate(A, zs, r0, nr + extra)
     return power_plane(F, True, last_is_end=ends)
+
+
+def correlate_half(A, zs, r0: int = 0, nr: int | None = None) -> np.ndarray:
+    """Correlation at half-bin resolution (2-bin Fourier interpolation,
+    Section 3 after Eq. f-interp): F[k, m] = sum over bins j with
+    |j - m/2| <= h_k of A_j conj(R_{z_k}(j - m/2)), for m = 2 r0 .. 2(r0+nr)-1,
+    A = 0 outside [0, nb).  Plain tap sum over the bins, numpy."""
+    A = np.asarray(A, np.complex128)
+    nb = A.shape[0]
+    if nr is None:
+        nr = nb - r0
+    zs = np.atleast_1d(np.asarray(zs, np.float64))
+    out = np.zeros((len(zs), 2 * nr), np.complex128)
+    base = r0 + np.arange(nr)
+    for kk, z in enumerate(zs):
+        h = half_width(z)
+        for e in (0, 1):               # m = 2 (r0 + i) + e, rho = r0 + i + e/2
+            acc = np.zeros(nr, np.complex128)
+            for q in range(-h, h + 2):   # bin j = r0 + i + q, offset d = q - e/2
+                d = q - e / 2.0
+                if abs(d) > h:
+                    continue
+                idx = base + q
+                ok = (idx >= 0) & (idx < nb)
+                Rd = complex(template_response(z, d))
+                acc[ok] += A[idx[ok]] * np.conj(Rd)
+            out[kk, e::2] = acc
+    return out
+
+
+def plane_interp2(A, zs, r0: int = 0, nr: int | None = None) -> np.ndarray:
+    """Plane of the 2-bin Fourier interpolation: column m = |F(m/2)|^2."""
+    return np.abs(correlate_half(A, zs, r0, nr)) ** 2
 
 
 def plane_points(A, zs, zi, col, interbin: bool = True) -> np.ndarray:

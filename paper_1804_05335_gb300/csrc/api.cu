@@ -88,13 +88,16 @@ int make_grid(const fdas_params* p, Grid* g) {
     if (p->zstep < 1 || p->zmin > p->zmax) return FDAS_E_INVAL;
     if ((int64_t)p->zmax - (int64_t)p->zmin > 100000) return FDAS_E_INVAL;
     if ((p->zmax - p->zmin) % p->zstep != 0) return FDAS_E_INVAL;
-    if (p->interbin != 0 && p->interbin != 1) return FDAS_E_INVAL;
+    if (p->interbin < 0 || p->interbin > 2) return FDAS_E_INVAL;
     int32_t zabs = abs(p->zmin) > abs(p->zmax) ? abs(p->zmin) : abs(p->zmax);
     int32_t hmax = half_width_i(zabs);
-    if (hmax > p->M / 2 - 1) return FDAS_E_INVAL;   // template must fit the discarded edge
+    // the template must fit the discarded edge: h taps each side (2h at half-bin
+    // sampling), plus the neighbour of the half bin
+    if (p->interbin == 2 ? 4 * hmax + 2 > p->M : hmax > p->M / 2 - 1) return FDAS_E_INVAL;
     g->K = (p->zmax - p->zmin) / p->zstep + 1;
     g->hmax = hmax;
-    g->sym = (p->zmin == -p->zmax && p->zmax > 0) ? 1 : 0;
+    // +-z conjugate pairing needs integer tap offsets: not with half-bin sampling
+    g->sym = (p->zmin == -p->zmax && p->zmax > 0 && p->interbin != 2) ? 1 : 0;
     if (g->sym) {
         int32_t j0 = 0;
         while (j0 < g->K && p->zmin + j0 * p->zstep < 0) ++j0;
@@ -110,11 +113,11 @@ int make_grid(const fdas_params* p, Grid* g) {
     return FDAS_OK;
 }
 
-int64_t series_items(const Grid& g, int L, int64_t nb) {
+int64_t series_items(const Grid& g, int L, int64_t npos) {
     int64_t items = 0;
     for (int k = 0; k < g.ng; ++k) {
         const int64_t B = L - g.gM[k];
-        items += ((nb + B - 1) / B) * g.gK[k];
+        items += ((npos + B - 1) / B) * g.gK[k];
     }
     return items;
 }
@@ -163,7 +166,7 @@ int64_t fdas_num_segments(const fdas_params* p, int64_t nb) {
     Grid g;
     if (make_grid(p, &g) != FDAS_OK || nb < 1) return FDAS_E_INVAL;
     int64_t B = p->L - p->M;
-    return (nb + B - 1) / B;
+    return (positions(p, nb) + B - 1) / B;
 }
 
 int32_t fdas_template_groups(const fdas_params* p, int32_t* overlap, int32_t* first_row,
@@ -243,6 +246,7 @@ int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, 
     Grid g;
     int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);
     if (rc != FDAS_OK) return rc;
+    if (prec != FDAS_PREC_FP32 && p->interbin == 2) return FDAS_E_UNSUPPORTED;
     if (prec == FDAS_PREC_FP32)
         return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
                                 reinterpret_cast<const float4*>(bank), plane, row_stride, fused,
@@ -265,7 +269,7 @@ int64_t fdas_batch_plan(const fdas_params* p, fdas_trial* trials, int32_t ntrial
         const int64_t width = p->interbin ? 2 * t.nb : t.nb;
         if (t.row_stride < width || (t.row_stride % 4) != 0) return FDAS_E_INVAL;
         t.item_begin = items;
-        items += series_items(g, p->L, t.nb);
+        items += series_items(g, p->L, positions(p, t.nb));
     }
     return items;
 }

@@ -185,6 +185,7 @@ __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
 struct SeriesState {
     const float2* spec;
     int64_t nb;
+    int64_t np;    // correlation positions: nb, or 2 nb with half-bin sampling
     float* plane;
     int64_t row_stride;
     int64_t end;   // first item of the next series
@@ -198,6 +199,7 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
         const fdas_trial& tr = A.trials[trial];
         st.spec = reinterpret_cast<const float2*>(tr.spec);
         st.nb = tr.nb;
+        st.np = A.interbin == 2 ? 2 * tr.nb : tr.nb;
         st.plane = tr.plane;
         st.row_stride = tr.row_stride;
         st.end = (trial + 1 < A.ntrials) ? A.trials[trial + 1].item_begin : A.items;
@@ -205,6 +207,7 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
     } else {
         st.spec = A.spec;
         st.nb = A.nb;
+        st.np = A.interbin == 2 ? 2 * A.nb : A.nb;
         st.plane = A.plane;
         st.row_stride = A.row_stride;
         st.end = A.items;
@@ -247,11 +250,11 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     // group, segment and template of the first item
     int grp = 0;
     int64_t rel = lo - first;
-    int64_t gseg = group_segments(A, L, 0, st.nb);
+    int64_t gseg = group_segments(A, L, 0, st.np);
     while (rel >= gseg * A.gK[grp] && grp + 1 < A.ng) {
         rel -= gseg * A.gK[grp];
         ++grp;
-        gseg = group_segments(A, L, grp, st.nb);
+        gseg = group_segments(A, L, grp, st.np);
     }
     M = A.gM[grp];
     B = L - M;
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 s = 0;
                 q = 0;
                 grp = 0;
-                gseg = group_segments(A, L, 0, st.nb);
+                gseg = group_segments(A, L, 0, st.np);
                 M = A.gM[0];
                 B = L - M;
                 NP = B / 2;
@@ -339,7 +342,12 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int64_t pos = base + i * T + t;
-                    v[i] = (pos >= 0 && pos < st.nb) ? __ldg(&st.spec[pos]) : make_float2(0.f, 0.f);
+                    if (A.interbin != 2) {
+                        v[i] = (pos >= 0 && pos < st.nb) ? __ldg(&st.spec[pos]) : make_float2(0.f, 0.f);
+                    } else {   // the spectrum with zeros interleaved (2-bin interpolation)
+                        v[i] = (pos >= 0 && pos < st.np && !(pos & 1)) ? __ldg(&st.spec[pos >> 1])
+                                                                       : make_float2(0.f, 0.f);
+                    }
                 }
                 forward_fft_d3<L>(v, buf0, buf1, t);
             } else {
@@ -482,9 +490,9 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
         const float2* o2 = outb + M / 2 + 2;
         float mx = 0.f;
-        if (r0 + B < st.nb) {
+        if (r0 + B < st.np) {
             constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
-            if (A.interbin) {
+            if (A.interbin == 1) {
 #pragma unroll
                 for (int u = 0; u < UMAX; ++u) {
                     const int p = t + u * T;
@@ -510,21 +518,21 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
             // segment reaching the end of the spectrum: per-bin checks
             for (int p = t; p < NP; p += T) {
                 const int64_t r = r0 + 2 * p;
-                if (r >= st.nb) break;
+                if (r >= st.np) break;
                 float4 pw = pair_powers(o4[p], o2[2 * p]);
-                if (r + 1 >= st.nb - 1) pw.w = 0.f;       // no bin r+2
-                if (r >= st.nb - 1) pw.y = 0.f;           // no bin r+1
-                if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
-                if (A.interbin) {
+                if (r + 1 >= st.np - 1) pw.w = 0.f;       // no bin r+2
+                if (r >= st.np - 1) pw.y = 0.f;           // no bin r+1
+                if (r + 1 >= st.np) { pw.z = 0.f; pw.w = 0.f; }
+                if (A.interbin == 1) {
                     plane_store1<OUT>(prow, 2 * r, pw.x);
                     plane_store1<OUT>(prow, 2 * r + 1, pw.y);
-                    if (r + 1 < st.nb) {
+                    if (r + 1 < st.np) {
                         plane_store1<OUT>(prow, 2 * r + 2, pw.z);
                         plane_store1<OUT>(prow, 2 * r + 3, pw.w);
                     }
                 } else {
                     plane_store1<OUT>(prow, r, pw.x);
-                    if (r + 1 < st.nb) plane_store1<OUT>(prow, r + 1, pw.z);
+                    if (r + 1 < st.np) plane_store1<OUT>(prow, r + 1, pw.z);
                     pw.y = 0.f;
                     pw.w = 0.f;
                 }
@@ -536,12 +544,12 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 // rare: rescan this thread's pairs and emit each crossing
                 for (int p = t; p < NP; p += T) {
                     const int64_t r = r0 + 2 * p;
-                    if (r >= st.nb) break;
+                    if (r >= st.np) break;
                     float4 pw = pair_powers(o4[p], o2[2 * p]);
-                    if (r + 1 >= st.nb - 1) pw.w = 0.f;
-                    if (r >= st.nb - 1) pw.y = 0.f;
-                    if (r + 1 >= st.nb) { pw.z = 0.f; pw.w = 0.f; }
-                    if (A.interbin) {
+                    if (r + 1 >= st.np - 1) pw.w = 0.f;
+                    if (r >= st.np - 1) pw.y = 0.f;
+                    if (r + 1 >= st.np) { pw.z = 0.f; pw.w = 0.f; }
+                    if (A.interbin == 1) {
                         if (pw.x > A.thr) emit(A, row, 2 * r, pw.x, st.flags);
                         if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y, st.flags);
                         if (pw.z > A.thr) emit(A, row, 2 * r + 2, pw.z, st.flags);
@@ -558,7 +566,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         q = q_next;
         if (grp_next != grp) {
             grp = grp_next;
-            gseg = group_segments(A, L, grp, st.nb);
+            gseg = group_segments(A, L, grp, st.np);
             M = A.gM[grp];
             B = L - M;
             NP = B / 2;

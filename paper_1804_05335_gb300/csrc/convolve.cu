@@ -30,7 +30,7 @@ int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, in
     a.nb = nb;
     a.plane = plane;
     a.row_stride = row_stride;
-    a.items = series_items(g, p->L, nb);
+    a.items = series_items(g, p->L, positions(p, nb));
     if (fused) {
         cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return FDAS_E_CUDA;

@@ -30,7 +30,7 @@ int launch_correlate_plane16(const fdas_params* p, const Grid& g, int type, cons
     a.nb = nb;
     a.plane = static_cast<float*>(plane);   // addressed as 16-bit elements by the kernel
     a.row_stride = row_stride;
-    a.items = series_items(g, p->L, nb);
+    a.items = series_items(g, p->L, positions(p, nb));
     if (fused) {
         cudaError_t e = cudaMemsetAsync(fused->count, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return FDAS_E_CUDA;

@@ -28,9 +28,13 @@ struct Grid {
 // Validates p; returns FDAS_OK and fills g (groups included), or FDAS_E_INVAL.
 int make_grid(const fdas_params* p, Grid* g);
 
-// Work items (segment, template) of one series of nb bins: for each group,
-// ceil(nb / (L - gM)) segments times gK templates.
-int64_t series_items(const Grid& g, int L, int64_t nb);
+// Positions of the correlation for nb spectral bins: nb, or 2 nb with
+// half-bin (2-bin Fourier interpolation) sampling.
+inline int64_t positions(const fdas_params* p, int64_t nb) { return p->interbin == 2 ? 2 * nb : nb; }
+
+// Work items (segment, template) of one series of npos positions: for each
+// group, ceil(npos / (L - gM)) segments times gK templates.
+int64_t series_items(const Grid& g, int L, int64_t npos);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_E_CUDA; }
 

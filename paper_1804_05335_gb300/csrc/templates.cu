@@ -16,22 +16,24 @@ namespace fdas {
 
 constexpr int kTapThreads = 128;
 
-// Kernel 1: one thread per (bank row b, offset d), d = -h..h.  Writes the
-// FIR kernel taps g[j] = conj(R_z(-j)) / L for j = -d to the start of bank
-// row b as tap index j + h (float2), where the row-b CTA of kernel 2 reads
-// them before it overwrites the row.
+// Kernel 1: one thread per (bank row b, tap j), |j| <= sub*h.  Writes the
+// FIR kernel taps g[j] = conj(R_z(-j/sub)) / L (sub = 1: one tap per bin;
+// sub = 2: half-bin sampling for 2-bin Fourier interpolation, the template
+// at twice the resolution) to the start of bank row b as tap index
+// j + sub*h (float2), where the row-b CTA of kernel 2 reads them before it
+// overwrites the row.
 __global__ void __launch_bounds__(kTapThreads) template_taps_kernel(int L, int zfirst, int zstep,
-                                                                    int width, int rows,
+                                                                    int width, int rows, int sub,
                                                                     float2* __restrict__ bank) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= rows * width) return;
     const int b = gid / width, idx = gid - b * width;
     const int z = zfirst + b * zstep;
     const int az = z < 0 ? -z : z;
-    const int h = (az + 1) / 2 + 8;
-    if (idx > 2 * h) return;
-    const int j = idx - h;                       // tap position (circular index j mod L)
-    const cd r = response<float>((double)z, (double)(-j));
+    const int hh = sub * ((az + 1) / 2 + 8);
+    if (idx > 2 * hh) return;
+    const int j = idx - hh;                      // tap position (circular index j mod L)
+    const cd r = response<float>((double)z, -(double)j / (double)sub);
     const double s = 1.0 / (double)L;
     bank[(size_t)b * (L + 16) + idx] = make_float2((float)(r.x * s), (float)(-r.y * s));
 }
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(kTapThreads) template_taps_kernel(int L, int z
 // placed kernel g (D1 distribution), forward FFT with the convolver's own
 // permutation-free transform, store the digit-reversed spectrum in place.
 template <int L>
-__global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zstep,
+__global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zstep, int sub,
                                                               float2* __restrict__ bank) {
     using S = ConvShape<L>;
     constexpr int T = S::T;
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zs
     const int b = blockIdx.x, t = threadIdx.x;
     const int z = zfirst + b * zstep;
     const int az = z < 0 ? -z : z;
-    const int h = (az + 1) / 2 + 8;
+    const int h = sub * ((az + 1) / 2 + 8);
     float2* row = bank + (size_t)b * S::ROW;
     float2 v[16];
 #pragma unroll
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zs
 }
 
 template <int L>
-static int launch_fft(int rows, int zfirst, int zstep, float2* bank, cudaStream_t st) {
+static int launch_fft(int rows, int zfirst, int zstep, int sub, float2* bank, cudaStream_t st) {
     constexpr size_t sm = 2 * ConvShape<L>::BUFS * sizeof(float2);
     static bool attr = false;
     if (!attr) {
@@ -88,23 +90,24 @@ static int launch_fft(int rows, int zfirst, int zstep, float2* bank, cudaStream_
             return FDAS_E_CUDA;
         attr = true;
     }
-    template_fft_kernel<L><<<rows, L / 16, sm, st>>>(zfirst, zstep, bank);
+    template_fft_kernel<L><<<rows, L / 16, sm, st>>>(zfirst, zstep, sub, bank);
     return cuda_status(cudaGetLastError());
 }
 
 int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st) {
-    const int width = 2 * g.hmax + 1;
+    const int sub = p->interbin == 2 ? 2 : 1;   // taps per bin
+    const int width = 2 * sub * g.hmax + 1;
     if (width > p->L + 16) return FDAS_E_UNSUPPORTED;
     const int zfirst = p->zmin + g.j0 * p->zstep;
     const int total = g.Kb * width;
     template_taps_kernel<<<(total + kTapThreads - 1) / kTapThreads, kTapThreads, 0, st>>>(
-        p->L, zfirst, p->zstep, width, g.Kb, bank);
+        p->L, zfirst, p->zstep, width, g.Kb, sub, bank);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return FDAS_E_CUDA;
     switch (p->L) {
-        case 1024: return launch_fft<1024>(g.Kb, zfirst, p->zstep, bank, st);
-        case 2048: return launch_fft<2048>(g.Kb, zfirst, p->zstep, bank, st);
-        case 4096: return launch_fft<4096>(g.Kb, zfirst, p->zstep, bank, st);
+        case 1024: return launch_fft<1024>(g.Kb, zfirst, p->zstep, sub, bank, st);
+        case 2048: return launch_fft<2048>(g.Kb, zfirst, p->zstep, sub, bank, st);
+        case 4096: return launch_fft<4096>(g.Kb, zfirst, p->zstep, sub, bank, st);
         default: return FDAS_E_INVAL;
     }
 }

@@ -48,7 +48,8 @@ def test_host_helpers():
 @pytest.mark.parametrize("bad", [
     dict(L=512), dict(L=3000), dict(M=60), dict(M=66), dict(M=4096),
     dict(zstep=0), dict(zmin=10, zmax=-10), dict(zmin=-5, zmax=6, zstep=2),
-    dict(interbin=2), dict(zmin=-300, zmax=300, M=256),          # h(300) = 158 > 127
+    dict(interbin=3), dict(zmin=-300, zmax=300, M=256),          # h(300) = 158 > 127
+    dict(interbin=2, M=256),                                     # 4 h(200) + 2 = 434 > 256
 ])
 def test_invalid_params_rejected(bad):
     kw = dict(L=2048, M=256, zmin=-200, zmax=200, zstep=2, interbin=1)
@@ -153,3 +154,15 @@ def test_template_groups_cover_the_grid_and_minimise_work(L, M, zmax, zstep):
 def test_template_groups_one_group_off_symmetric_grids():
     p = F.params(2048, 128, -10, 30, 5, 1)
     assert F.fdas_template_groups(p) == [(128, 0, F.fdas_num_templates(p))]
+
+
+def test_interp2_grid_and_split_rejection():
+    p = F.params(2048, 436, -200, 200, 2, 2)           # 4 h(200) + 2 = 434 <= 436
+    assert F.fdas_num_templates(p) == 201
+    assert F.fdas_bank_rows(p) == 201                   # no +-z pairing at half-bin taps
+    assert F.fdas_plane_width(p, 1 << 22) == 1 << 23
+    assert F.fdas_num_segments(p, 1 << 22) == -(-(1 << 23) // (2048 - 436))
+    assert F.fdas_template_groups(p) == [(436, 0, 201)]
+    with pytest.raises(F.FdasError) as e:
+        F.fdas_correlate_split(p, 1, 256, 1000, 256, 256, 2000, stream=0)
+    assert e.value.code == F.FDAS_E_UNSUPPORTED

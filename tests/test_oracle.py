@@ -320,3 +320,43 @@ def test_refine_ascent_finds_an_injected_chirp():
     r, z, P = O.refine_ascent(A, 3000.5, 8.0, m=O.half_width(20), steps=20)
     assert abs(r - r0) < 0.05 and abs(z - z0) < 0.3
     assert P > O.refine_power(A, 3000.5, 8.0, O.half_width(20))[0]
+
+
+# ---------------------------------------------------------------- 2-bin Fourier interpolation
+def test_half_bin_correlation_even_columns_are_the_integer_tap_sum():
+    A = synth.random_spectrum(900, 12).astype(np.complex128)
+    zs = O.z_grid(-12, 12, 4)
+    Fh = O.correlate_half(A, zs)
+    F = O.correlate(A, zs)
+    assert np.abs(Fh[:, 0::2] - F).max() < 1e-12
+
+
+def test_half_bin_correlation_recovers_a_matched_half_bin_template():
+    # noise-free spectrum A_k = R_z0(k - rho0) at a half-integer rho0: F(rho0)
+    # is the template energy over the window (Cauchy-Schwarz equality)
+    for z0 in (0.0, 6.0, -14.0):
+        rho0 = 300.5
+        k = np.arange(700)
+        A = O.template_response(z0, k - rho0)
+        h = O.half_width(z0)
+        m0 = int(2 * rho0)
+        Fh = O.correlate_half(A, [z0], 280, 40)[0]
+        d = np.arange(-h, h + 1) - 0.5
+        d = d[np.abs(d) <= h]
+        energy = np.sum(np.abs(O.template_response(z0, d)) ** 2)
+        F0 = Fh[m0 - 2 * 280]
+        assert abs(F0 - energy) < 1e-12 * energy
+
+
+def test_half_bin_correlation_matches_quadrature_responses():
+    # the odd columns again, with R from Gauss-Legendre quadrature of its integral
+    A = synth.random_spectrum(400, 13).astype(np.complex128)
+    for z in (10.0, -3.0, 0.0):
+        h = O.half_width(z)
+        Fh = O.correlate_half(A, [z], 100, 50)[0]
+        for i in (0, 17, 49):
+            rho = 100 + i + 0.5
+            j = np.arange(int(np.ceil(rho - h)), int(np.floor(rho + h)) + 1)
+            R, _, _ = O.response_derivs_quadrature(z, j - rho)
+            ref = np.sum(A[j] * np.conj(R))
+            assert abs(Fh[2 * i + 1] - ref) < 1e-9 * (1 + abs(ref))
