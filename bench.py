@@ -429,6 +429,53 @@ def interp2_row(args, torch, dev, S, wl):
                            "mean_by_frequency_offset": byfrac}}
 
 
+def harmonic_row(args, torch, dev, S, wl):
+    """Harmonic sums H = 2, 4, 8 with fused thresholds on the production plane
+    (FP32, and binary16 from fdas_correlate_plane16): time, useful bytes read
+    (one element per harmonic per fundamental that has it) over time, and the
+    candidates per level."""
+    from paper_1804_05335_gb300 import (FDAS_PLANE_F16, fdas_correlate_plane16,
+                                        fdas_harmonic_sum)
+    peak, _ = measured_peak()
+    thr = [40.0, 60.0, 90.0]
+    K, W = S.K, S.width
+    j0 = wl.zmin // wl.zstep
+    useful = 0
+    for lev, H in enumerate((2, 4, 8)):
+        rows = sum(1 for j in range(K)
+                   if all(0 <= (h - 1) * j0 + h * j < K for h in range(1, H + 1)))
+        cols = (W - 1) // H + 1
+        useful += rows * cols * (2 if lev < 2 else 4)     # harmonics added at this level
+    cap = 1 << 16
+    out = torch.empty(4 * cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    plane16 = torch.empty(K * S.row_stride, dtype=torch.float16, device=dev)
+    fdas_correlate_plane16(S.p, FDAS_PLANE_F16, S.spec, S.nb, S.bank, plane16, S.row_stride,
+                           None, S.status)
+    S.correlate(fused=False)
+    res = {}
+    reps = 10
+    for name, ptype, pl, esize in (("f32", 0, S.plane, 4), ("f16", 1, plane16, 2)):
+        def run():
+            fdas_harmonic_sum(S.p, ptype, pl, W, S.row_stride, thr, out, cap, cnt, S.status)
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        k = min(int(cnt.item()), cap)
+        h = out[: 4 * k].view(k, 4)[:, 3].cpu().numpy()
+        res[name] = {"ms": ms, "useful_bytes": useful * esize,
+                     "useful_gbs": useful * esize / (ms / 1e3) / 1e9,
+                     "useful_frac_of_peak": useful * esize / (ms / 1e3) / 1e9 / peak,
+                     "candidates": {str(H): int((h == H).sum()) for H in (2, 4, 8)}}
+    del plane16
+    return {"thresholds": {"2": thr[0], "4": thr[1], "8": thr[2]}, "planes": res}
+
+
 def split_row(args, torch, dev, S, wl):
     """The production plane with the four radix-16 DFT passes of every segment
     FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
@@ -638,6 +685,7 @@ def run_native(args):
             line["rows"] = {"a9_split": split_row(args, torch, dev, S, wl)}
             line["rows"]["f1_plane16"] = plane16_row(args, torch, dev, S, wl)
             line["rows"]["f2_interp2"] = interp2_row(args, torch, dev, S, wl)
+            line["rows"]["f3_harmonic"] = harmonic_row(args, torch, dev, S, wl)
             line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()

@@ -267,6 +267,27 @@ int fdas_correlate_plane16(const fdas_params *p, int32_t type, const float *spec
                            const float *bank, void *plane, int64_t row_stride,
                            const fdas_fused_threshold *fused, int32_t *status, void *stream);
 
+/*
+ * fdas_harmonic_sum -- incremental harmonic sums of the plane with a fused
+ * threshold (the search stage after the plane: a periodic signal with
+ * fundamental (r, z) has its h-th harmonic at (h r, h z); Sections 3 and 7).
+ * For every fundamental (row j, column c) whose harmonics lie on the plane:
+ *   S_H(j, c) = sum_{h=1}^{H} plane[(h - 1) zmin/zstep + h j][h c],
+ * for H = 2, 4, 8 (levels 1..nlevels), since column h c holds h r and row
+ * (h - 1) zmin/zstep + h j holds h z_j.  A fundamental stops at the first
+ * level whose harmonics leave the plane.  Every S_H > thr[level - 1] is
+ * listed as a fdas_cand (z_idx = j, col = c, power = S_H, flags = H), in no
+ * particular order; count (device) is reset by the call and ends holding the
+ * number found, which may exceed cap (FDAS_STATUS_OVERFLOW then set).
+ * plane_type: 0 (float), FDAS_PLANE_F16 or FDAS_PLANE_BF16.
+ * plane: (device) fdas_num_templates(p) rows of row_stride elements; width
+ *   columns (fdas_plane_width).  thr: (host) nlevels thresholds, nlevels 1..3.
+ * Errors: FDAS_E_INVAL (bad params or pointers, zmin not a multiple of zstep).
+ */
+int fdas_harmonic_sum(const fdas_params *p, int32_t plane_type, const void *plane, int64_t width,
+                      int64_t row_stride, int32_t nlevels, const float *thr, fdas_cand *out,
+                      int32_t cap, int32_t *count, int32_t *status, void *stream);
+
 /* Arithmetic of the convolver's radix-16 DFT passes (fdas_correlate_split). */
 #define FDAS_PREC_FP32 0        /* FP32 on the CUDA cores, as fdas_correlate */
 #define FDAS_PREC_FP16_SPLIT 1  /* FP16 hi+lo operands on tensor cores, FP32 accumulation */

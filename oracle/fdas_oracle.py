@@ -58,7 +58,7 @@ __all__ = [
     "real_spectrum", "normalise", "block_medians", "correlate", "correlate_points",
     "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
     "search", "oracle_threads", "PEAK_FLAG", "response_derivs_quadrature", "refine_taps",
-    "correlate_half", "plane_interp2",
+    "correlate_half", "plane_interp2", "harmonic_sum", "harmonic_candidates",
     "refine_power", "refine_grad_spec", "refine_ascent",
 ]
 
@@ -354,6 +354,37 @@ def correlate_half(A, zs, r0: int = 0, nr: int | None = None) -> np.ndarray:
 def plane_interp2(A, zs, r0: int = 0, nr: int | None = None) -> np.ndarray:
     """Plane of the 2-bin Fourier interpolation: column m = |F(m/2)|^2."""
     return np.abs(correlate_half(A, zs, r0, nr)) ** 2
+
+
+def harmonic_sum(P, zmin: int, zstep: int, H: int) -> np.ndarray:
+    """S[j, c] = sum_{h=1}^{H} P[(h-1) zmin/zstep + h j, h c]: the powers at
+    (h r, h z_j) summed over the first H harmonics, for every fundamental
+    (j, c) whose H harmonics all lie on the plane (row in range, h c < width);
+    NaN elsewhere.  Row j holds z_j = zmin + j zstep (zmin a multiple of zstep)."""
+    P = np.asarray(P, np.float64)
+    K, W = P.shape
+    j0 = zmin // zstep
+    S = np.full((K, W), np.nan)
+    for j in range(K):
+        rows = [(h - 1) * j0 + h * j for h in range(1, H + 1)]
+        if min(rows) < 0 or max(rows) >= K:
+            continue
+        nc = (W - 1) // H + 1            # columns c with H c < W
+        c = np.arange(nc)
+        S[j, :nc] = sum(P[rows[h - 1], h * c] for h in range(1, H + 1))
+    return S
+
+
+def harmonic_candidates(P, zmin: int, zstep: int, thresholds):
+    """(rows, cols, sums, H) with S_H > thresholds[level] for H = 2, 4, 8, for
+    fundamentals whose second harmonic is on the plane; sorted by (H, row, col)."""
+    out = []
+    for lev, thr in enumerate(thresholds):
+        H = 2 << lev
+        S = harmonic_sum(P, zmin, zstep, H)
+        j, c = np.nonzero(np.nan_to_num(S, nan=-np.inf) > thr)
+        out.append((j, c, S[j, c], np.full(len(j), H)))
+    return tuple(np.concatenate([o[i] for o in out]) for i in range(4))
 
 
 def plane_points(A, zs, zi, col, interbin: bool = True) -> np.ndarray:

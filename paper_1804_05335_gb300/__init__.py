@@ -18,7 +18,7 @@ __all__ = [
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
-    "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16",
+    "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16", "fdas_harmonic_sum",
     "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
@@ -115,6 +115,8 @@ def load_library():
                                                 c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_correlate_plane16": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
                                                   c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
+        "fdas_harmonic_sum": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_i64, c_i32,
+                                             c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
         "fdas_batch_plan": (c_i64, [P(fdas_params), P(fdas_trial), c_i32]),
@@ -265,6 +267,16 @@ def fdas_correlate_plane16(p: fdas_params, ptype: int, spec, nb: int, bank, plan
                                                  int(nb), _ptr(bank), _ptr(plane),
                                                  int(row_stride), f, _ptr(status),
                                                  _stream(stream)), "fdas_correlate_plane16")
+
+
+def fdas_harmonic_sum(p: fdas_params, plane_type: int, plane, width: int, row_stride: int,
+                      thresholds, out, cap: int, count, status=None, stream=None) -> None:
+    """Harmonic sums H = 2, 4, 8 (one threshold per level) with candidates in out."""
+    thr = (c_f32 * 3)(*[float(v) for v in thresholds])
+    _check(load_library().fdas_harmonic_sum(ctypes.byref(p), int(plane_type), _ptr(plane),
+                                            int(width), int(row_stride), len(thresholds), thr,
+                                            _ptr(out), int(cap), _ptr(count), _ptr(status),
+                                            _stream(stream)), "fdas_harmonic_sum")
 
 
 def fdas_correlate_split(p: fdas_params, prec: int, spec, nb: int, bank, plane, row_stride: int,

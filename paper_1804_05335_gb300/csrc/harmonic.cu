@@ -1,0 +1,147 @@
+// fdas_harmonic_sum: incremental harmonic summing on the f-fdot plane with a
+// fused threshold (the search stage after the plane that the paper names as
+// the next to move on chip, Sections 3 and 7).
+//
+// A periodic signal with fundamental (r, z) has its h-th harmonic at (h r,
+// h z).  On the plane, row j holds z_j = zmin + j zstep and column c holds
+// r = c/2 (interbinned) or r = c, so harmonic h of (j, c) sits at column h c
+// and at row j_h = (h - 1) zmin / zstep + h j, which is a grid row whenever
+// zmin is a multiple of zstep.  For every fundamental whose second harmonic
+// is on the plane, one thread forms
+//   S_2 = P[j][c] + P[j_2][2c],  S_4 = S_2 + P[j_3][3c] + P[j_4][4c],
+//   S_8 = S_4 + P[j_5][5c] + ... + P[j_8][8c],
+// stopping at the first level whose harmonics leave the plane, and lists
+// (row j, column c, S_H, H) for every S_H above that level's threshold.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace fdas {
+
+constexpr int kHarmThreads = 256;
+
+template <int TYPE>
+__device__ __forceinline__ float plane_load(const void* plane, int64_t i) {
+    if constexpr (TYPE == 0) {
+        return __ldg(static_cast<const float*>(plane) + i);
+    } else if constexpr (TYPE == 1) {
+        return __half2float(__ldg(static_cast<const __half*>(plane) + i));
+    } else {
+        return __bfloat162float(__ldg(static_cast<const __nv_bfloat16*>(plane) + i));
+    }
+}
+
+struct HarmArgs {
+    const void* plane;
+    int64_t width, row_stride;
+    int32_t K, j0h;          // plane rows; j0h = zmin / zstep (row offset of harmonic rows)
+    int32_t nlev;            // levels: 1 -> H = 2, 2 -> up to 4, 3 -> up to 8
+    float thr[3];
+    fdas_cand* out;
+    int32_t cap;
+    int32_t* count;
+    int32_t* status;
+};
+
+__device__ __forceinline__ void harm_emit(const HarmArgs& A, int row, int64_t col, float v, int H) {
+    const int idx = atomicAdd(A.count, 1);
+    if (idx < A.cap) {
+        fdas_cand c;
+        c.z_idx = row;
+        c.col = (int32_t)col;
+        c.power = v;
+        c.flags = H;
+        A.out[idx] = c;
+    } else if (A.status) {
+        atomicOr(A.status, FDAS_STATUS_OVERFLOW);
+    }
+}
+
+// grid: x over columns, y over the fundamental rows with a second harmonic.
+// Harmonic rows j_h = h (j + j0h) - j0h are linear in h, so the harmonics up
+// to H are all on the plane when j_H is; each thread issues every load of its
+// levels at once and then forms the running sums.
+template <int TYPE>
+__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo) {
+    const int64_t c = (int64_t)blockIdx.x * kHarmThreads + threadIdx.x;
+    const int j = jlo + (int)blockIdx.y;
+    if (2 * c >= A.width) return;
+    int nl = 0;   // levels whose harmonic rows and columns are on the plane
+    for (int lev = 0; lev < A.nlev; ++lev) {
+        const int H = 2 << lev;
+        const int jH = (H - 1) * A.j0h + H * j;
+        if (jH < 0 || jH >= A.K || (int64_t)H * c >= A.width) break;
+        nl = lev + 1;
+    }
+    float v[8];
+#pragma unroll
+    for (int h = 1; h <= 8; ++h) {
+        const int need = h <= 2 ? 1 : (h <= 4 ? 2 : 3);
+        v[h - 1] = 0.f;
+        if (need <= nl) {
+            const int jh = (h - 1) * A.j0h + h * j;
+            v[h - 1] = plane_load<TYPE>(A.plane, (int64_t)jh * A.row_stride + (int64_t)h * c);
+        }
+    }
+    float s = v[0] + v[1];
+    if (s > A.thr[0]) harm_emit(A, j, c, s, 2);
+    if (nl < 2) return;
+    s += v[2] + v[3];
+    if (s > A.thr[1]) harm_emit(A, j, c, s, 4);
+    if (nl < 3) return;
+    s += (v[4] + v[5]) + (v[6] + v[7]);
+    if (s > A.thr[2]) harm_emit(A, j, c, s, 8);
+}
+
+}  // namespace fdas
+
+using namespace fdas;
+
+extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const void* plane,
+                                 int64_t width, int64_t row_stride, int32_t nlevels,
+                                 const float* thr, fdas_cand* out, int32_t cap, int32_t* count,
+                                 int32_t* status, void* stream) {
+    Grid g;
+    int rc = make_grid(p, &g);
+    if (rc != FDAS_OK) return rc;
+    if (plane_type < 0 || plane_type > 2 || !plane || !thr || !out || !count) return FDAS_E_INVAL;
+    if (nlevels < 1 || nlevels > 3 || width < 1 || row_stride < width || cap < 0)
+        return FDAS_E_INVAL;
+    if (p->zmin % p->zstep != 0) return FDAS_E_INVAL;   // harmonic rows must be grid rows
+    if (!aligned(plane, plane_type == 0 ? 4 : 2) || !aligned(out, 4) || !aligned(count, 4))
+        return FDAS_E_INVAL;
+    if (status && !aligned(status, 4)) return FDAS_E_INVAL;
+    HarmArgs a;
+    a.plane = plane;
+    a.width = width;
+    a.row_stride = row_stride;
+    a.K = g.K;
+    a.j0h = p->zmin / p->zstep;
+    a.nlev = nlevels;
+    for (int l = 0; l < 3; ++l) a.thr[l] = l < nlevels ? thr[l] : 0.f;
+    a.out = out;
+    a.cap = cap;
+    a.count = count;
+    a.status = status;
+    // fundamental rows whose second harmonic row 2 j + j0h lies in [0, K)
+    int jlo = 0, jhi = -1;
+    for (int j = 0; j < g.K; ++j) {
+        const int j2 = a.j0h + 2 * j;
+        if (j2 >= 0 && j2 < g.K) {
+            if (jhi < 0) jlo = j;
+            jhi = j;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
+    if (jhi < 0) return FDAS_OK;
+    const int64_t nc = (width + 1) / 2;
+    const dim3 grid((unsigned)((nc + kHarmThreads - 1) / kHarmThreads), (unsigned)(jhi - jlo + 1));
+    switch (plane_type) {
+        case 0: harmonic_kernel<0><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
+        case 1: harmonic_kernel<1><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
+        default: harmonic_kernel<2><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
+    }
+    return cuda_status(cudaGetLastError());
+}

@@ -166,3 +166,21 @@ def test_interp2_grid_and_split_rejection():
     with pytest.raises(F.FdasError) as e:
         F.fdas_correlate_split(p, 1, 256, 1000, 256, 256, 2000, stream=0)
     assert e.value.code == F.FDAS_E_UNSUPPORTED
+
+
+def test_harmonic_sum_rejects_bad_arguments_before_launch():
+    p = F.params(2048, 256, -200, 200, 2, 1)
+    cases = [
+        lambda: F.fdas_harmonic_sum(p, 3, 256, 1000, 1000, [20.0], 256, 4, 256, stream=0),     # type
+        lambda: F.fdas_harmonic_sum(p, 0, 0, 1000, 1000, [20.0], 256, 4, 256, stream=0),       # NULL plane
+        lambda: F.fdas_harmonic_sum(p, 0, 256, 1000, 999, [20.0], 256, 4, 256, stream=0),      # stride
+        lambda: F.fdas_harmonic_sum(p, 0, 256, 1000, 1000, [], 256, 4, 256, stream=0),         # no level
+        lambda: F.fdas_harmonic_sum(p, 0, 256, 1000, 1000, [1.0] * 4, 256, 4, 256, stream=0),  # 4 levels
+        lambda: F.fdas_harmonic_sum(F.params(2048, 256, -21, 21, 2, 1), 0, 256, 1000, 1000,
+                                    [20.0], 256, 4, 256, stream=0),                            # zmin % zstep
+    ]
+    for f in cases:
+        with pytest.raises((F.FdasError, ValueError, IndexError)) as e:
+            f()
+        if isinstance(e.value, F.FdasError):
+            assert e.value.code == F.FDAS_E_INVAL

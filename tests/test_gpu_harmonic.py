@@ -1,0 +1,90 @@
+"""fdas_harmonic_sum against the oracle's harmonic sums on the same plane
+values (FP32 and 16-bit planes): identical candidate lists except sums within
+a relative 1e-5 of a threshold (FP32 against FP64 summation)."""
+import numpy as np
+import pytest
+
+import oracle.fdas_oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_05335_gb300 as F
+    F.load_library()
+    return F
+
+
+def _run(F, p, plane_dev, ptype, width, stride, thr, cap=1 << 16):
+    out = torch.zeros(4 * cap, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    F.fdas_harmonic_sum(p, ptype, plane_dev, width, stride, thr, out, cap, count, status)
+    k = int(count.item())
+    a = out[: 4 * min(k, cap)].view(-1, 4).cpu().numpy()
+    return a, k, int(status.item())
+
+
+def _compare(a, ref, thr):
+    rr, cc, ss, hh = ref
+    got = {(int(h), int(r), int(c)): float(np.frombuffer(np.int32(v).tobytes(), np.float32)[0])
+           for r, c, v, h in a}
+    exp = {(int(h), int(r), int(c)): float(s) for r, c, s, h in zip(rr, cc, ss, hh)}
+    lev = {2: 0, 4: 1, 8: 2}
+    for key in set(got) ^ set(exp):
+        v = got.get(key, exp.get(key))
+        t = thr[lev[key[0]]]
+        assert abs(v - t) <= 1e-5 * t, ("lists differ at", key, v)
+    for key in set(got) & set(exp):
+        assert abs(got[key] - exp[key]) <= 1e-5 * exp[key], key
+
+
+@pytest.mark.parametrize("ptype", [0, 1, 2], ids=["f32", "f16", "bf16"])
+def test_harmonic_sum_matches_oracle_on_random_plane(F, ptype):
+    p = F.params(2048, 256, -40, 40, 2, 1)
+    K = F.fdas_num_templates(p)
+    width, stride = 20002, 20004
+    rng = np.random.default_rng(60 + ptype)
+    P = rng.exponential(1.0, (K, width)).astype(np.float32)
+    P[20, 300] = P[30, 600] = 25.0          # a planted fundamental (z = 0, col 300) at H = 2
+    dt = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}[ptype]
+    dev = torch.zeros((K, stride), dtype=dt, device="cuda")
+    dev[:, :width] = torch.from_numpy(P).to(dt)
+    Pq = dev[:, :width].float().cpu().numpy().astype(np.float64)   # the values the kernel reads
+    thr = [14.0, 22.0, 36.0]
+    a, k, st = _run(F, p, dev, ptype, width, stride, thr)
+    assert st == 0 and k == len(a) and k > 0
+    _compare(a, O.harmonic_candidates(Pq, -40, 2, thr), thr)
+    assert any(int(h) == 2 and int(r) == 20 and int(c) == 300 for r, c, v, h in a)
+
+
+def test_harmonic_sum_on_a_searched_plane_finds_the_fundamental(F):
+    from paper_1804_05335_gb300.search import Search
+    n, r0, z0 = 1 << 16, 2000.0, 6.0
+    x = synth.make_series(n, tuple((h * r0, h * z0, 7.0) for h in range(1, 5)), 61)
+    S = Search(n, 2048, 256, -40, 40, 2)
+    S.series.copy_(torch.from_numpy(x))
+    S.step()
+    thr = [30.0, 50.0]
+    a, k, st = _run(F, S.p, S.plane, 0, S.width, S.row_stride, thr)
+    assert st == 0
+    P = S.plane2d().cpu().numpy().astype(np.float64)
+    _compare(a, O.harmonic_candidates(P, -40, 2, thr), thr)
+    best = max((v for r, c, v, h in a if int(h) == 4), key=lambda v: np.int32(v).view(np.float32),
+               default=None)
+    assert best is not None
+    top = [(int(r), int(c)) for r, c, v, h in a if int(h) == 4 and v == best][0]
+    assert top[0] == int((z0 + 40) // 2) and abs(top[1] / 2.0 - r0) <= 0.5
+
+
+def test_harmonic_sum_overflow_keeps_the_count(F):
+    p = F.params(2048, 256, -20, 20, 2, 1)
+    K = F.fdas_num_templates(p)
+    P = torch.full((K, 4000), 10.0, dtype=torch.float32, device="cuda")
+    a, k, st = _run(F, p, P, 0, 4000, 4000, [5.0], cap=16)
+    assert k > 16 and len(a) == 16 and (st & 2)

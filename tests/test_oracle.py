@@ -360,3 +360,54 @@ def test_half_bin_correlation_matches_quadrature_responses():
             R, _, _ = O.response_derivs_quadrature(z, j - rho)
             ref = np.sum(A[j] * np.conj(R))
             assert abs(Fh[2 * i + 1] - ref) < 1e-9 * (1 + abs(ref))
+
+
+# ---------------------------------------------------------------- harmonic summing
+def test_harmonic_sum_brute_force_tiny():
+    rng = np.random.default_rng(14)
+    zmin, zstep, K, W = -12, 3, 9, 37            # z = -12..12 step 3
+    P = rng.exponential(1.0, (K, W))
+    for H in (2, 4, 8):
+        S = O.harmonic_sum(P, zmin, zstep, H)
+        for j in range(K):
+            for c in range(W):
+                tot, ok = 0.0, True
+                for h in range(1, H + 1):
+                    z = h * (zmin + j * zstep)
+                    row = (z - zmin) / zstep
+                    if not (0 <= row < K) or h * c >= W:
+                        ok = False
+                        break
+                    tot += P[int(row), h * c]
+                if ok:
+                    assert abs(S[j, c] - tot) < 1e-12
+                else:
+                    assert np.isnan(S[j, c])
+
+
+def test_harmonic_sum_peaks_at_an_injected_pulse_trains_fundamental():
+    # four harmonically related chirps (h r0, h z0): the 4-harmonic sum peaks
+    # at the fundamental, where no single harmonic stands out
+    n, r0, z0 = 1 << 15, 1000.0, 4.0
+    inj = tuple((h * r0, h * z0, 6.0) for h in range(1, 5))
+    x = synth.make_series(n, inj, 51)
+    A = O.normalise(O.real_spectrum(x), 1024)
+    zmin, zstep = -20, 2
+    P = O.plane(A, O.z_grid(zmin, 20, 2))
+    S = O.harmonic_sum(P, zmin, zstep, 4)
+    j0 = int((z0 - zmin) // zstep)
+    k, c = np.unravel_index(np.nanargmax(S), S.shape)
+    assert k == j0 and abs(c / 2.0 - r0) <= 0.5
+    assert S[k, c] > 2 * np.nanmax(P[:, 2 * int(r0) - 4: 2 * int(r0) + 5])
+
+
+def test_harmonic_sum_of_noise_adds_the_mean_powers():
+    x = synth.make_series(1 << 16, (), 52)
+    A = O.normalise(O.real_spectrum(x), 1024)
+    P = O.plane(A, O.z_grid(-4, 4, 2))
+    S2 = O.harmonic_sum(P, -4, 2, 2)
+    # even columns: full bins only; the fundamental row of z = 0 sums rows 2 and 2
+    m_full = P[:, 0::2].mean()
+    s = S2[2, 0::2]
+    s = s[~np.isnan(s)]
+    assert abs(s.mean() - 2 * m_full) < 0.03 * 2 * m_full
