@@ -476,6 +476,50 @@ def harmonic_row(args, torch, dev, S, wl):
     return {"thresholds": {"2": thr[0], "4": thr[1], "8": thr[2]}, "planes": res}
 
 
+def significance_row(args, torch, dev, S, wl):
+    """Noise statistics of the production plane against the model of
+    fdas_noise_means: empirical over predicted mean power of even (full bin)
+    and odd (half bin) columns on 21 rows, points above the threshold against
+    the noise expectation, and the single-trial sigma of each injection."""
+    from paper_1804_05335_gb300 import fdas_noise_means
+    from paper_1804_05335_gb300.significance import point_significance
+    m = torch.empty(2 * S.K, dtype=torch.float32, device=dev)
+    fdas_noise_means(S.p, m)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fdas_noise_means(S.p, m)
+    e1.record()
+    torch.cuda.synchronize()
+    mu = m.view(S.K, 2).cpu().numpy().astype(np.float64)
+    S.correlate(fused=True)
+    _, _, _, _, ncand = S.candidates()
+    P = S.plane2d()
+    ratios = []
+    for k in range(0, S.K, 10):
+        row = P[k]
+        ratios.append((float(row[0::2].double().mean()) / mu[k, 0],
+                       float(row[1::2].double().mean()) / mu[k, 1]))
+    ratios = np.array(ratios)
+    half = S.width // 2
+    expect = float(np.sum(half * (np.exp(-wl.threshold / mu[:, 0]) + np.exp(-wl.threshold / mu[:, 1]))))
+    zs = np.arange(wl.zmin, wl.zmax + 1, wl.zstep)
+    inj = []
+    for r0, z0, snr in wl.injections:
+        k0 = int(np.argmin(np.abs(zs - z0)))
+        ks = slice(max(0, k0 - 2), k0 + 3)
+        cs = slice(2 * int(r0) - 16, 2 * int(r0) + 16)
+        a = P[ks, cs].cpu().numpy()
+        k, c = np.unravel_index(np.argmax(a), a.shape)
+        _, sig = point_significance(a[k, c], mu[ks.start + k, (cs.start + c) & 1])
+        inj.append({"snr": snr, "peak_power": float(a[k, c]), "sigma_single_trial": float(sig[0])})
+    return {"means_kernel_ms": e0.elapsed_time(e1),
+            "mean_ratio_even": {"min": float(ratios[:, 0].min()), "max": float(ratios[:, 0].max())},
+            "mean_ratio_odd": {"min": float(ratios[:, 1].min()), "max": float(ratios[:, 1].max())},
+            "points_above_threshold": int(ncand), "noise_expectation": expect,
+            "injections": inj}
+
+
 def split_row(args, torch, dev, S, wl):
     """The production plane with the four radix-16 DFT passes of every segment
     FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
@@ -686,6 +730,7 @@ def run_native(args):
             line["rows"]["f1_plane16"] = plane16_row(args, torch, dev, S, wl)
             line["rows"]["f2_interp2"] = interp2_row(args, torch, dev, S, wl)
             line["rows"]["f3_harmonic"] = harmonic_row(args, torch, dev, S, wl)
+            line["rows"]["f4_significance"] = significance_row(args, torch, dev, S, wl)
             line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()

@@ -288,6 +288,22 @@ int fdas_harmonic_sum(const fdas_params *p, int32_t plane_type, const void *plan
                       int64_t row_stride, int32_t nlevels, const float *thr, fdas_cand *out,
                       int32_t cap, int32_t *count, int32_t *status, void *stream);
 
+/*
+ * fdas_noise_means -- mean power of pure noise in every plane row, for
+ * significances (the paper leaves the statistics of single-bin, interbinned
+ * and Fourier-interpolated powers open, Section 5.2).  With the normalised
+ * spectrum unit-variance complex Gaussian noise, every plane value is
+ * exponential: P(power > x) = exp(-x / mean).
+ *   means[2j]   : even columns (full bins; integer positions with interbin 2)
+ *                 sum_{|d|<=h} |R(d)|^2
+ *   means[2j+1] : odd columns: interbin 1 half bins (pi/4)^2 sum_d |Rt(d) -
+ *                 Rt(d-1)|^2 (Rt = R on |d| <= h, 0 outside); interbin 2
+ *                 half-integer positions sum_{|d|<=h-1/2} |R(d)|^2; interbin 0
+ *                 the full-bin mean again.
+ * Row j holds z_j = zmin + j*zstep; R in FP64.  means: (device) 2 K floats.
+ */
+int fdas_noise_means(const fdas_params *p, float *means, void *stream);
+
 /* Arithmetic of the convolver's radix-16 DFT passes (fdas_correlate_split). */
 #define FDAS_PREC_FP32 0        /* FP32 on the CUDA cores, as fdas_correlate */
 #define FDAS_PREC_FP16_SPLIT 1  /* FP16 hi+lo operands on tensor cores, FP32 accumulation */

@@ -58,7 +58,7 @@ __all__ = [
     "real_spectrum", "normalise", "block_medians", "correlate", "correlate_points",
     "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
     "search", "oracle_threads", "PEAK_FLAG", "response_derivs_quadrature", "refine_taps",
-    "correlate_half", "plane_interp2", "harmonic_sum", "harmonic_candidates",
+    "correlate_half", "plane_interp2", "harmonic_sum", "harmonic_candidates", "noise_means",
     "refine_power", "refine_grad_spec", "refine_ascent",
 ]
 
@@ -385,6 +385,29 @@ def harmonic_candidates(P, zmin: int, zstep: int, thresholds):
         j, c = np.nonzero(np.nan_to_num(S, nan=-np.inf) > thr)
         out.append((j, c, S[j, c], np.full(len(j), H)))
     return tuple(np.concatenate([o[i] for o in out]) for i in range(4))
+
+
+def noise_means(zs, interbin: int = 1) -> np.ndarray:
+    """(K, 2): mean power of unit complex Gaussian noise in the even and odd
+    columns of each row (the variance of the correlated amplitude):
+    even: sum_{|d|<=h} |R(d)|^2;  odd, interbin 1: (pi/4)^2 sum_d |Rt(d) -
+    Rt(d-1)|^2 with Rt = R on |d| <= h and 0 outside; odd, interbin 2:
+    sum over half-integer |d| <= h - 1/2 of |R(d)|^2; odd, interbin 0: as even."""
+    zs = np.atleast_1d(np.asarray(zs, np.float64))
+    out = np.zeros((len(zs), 2))
+    for k, z in enumerate(zs):
+        h = half_width(z)
+        R = template_response(z, np.arange(-h, h + 1, dtype=np.float64))
+        full = np.sum(np.abs(R) ** 2)
+        if interbin == 1:
+            Rt = np.concatenate([[0.0], R, [0.0]])
+            odd = (np.pi / 4) ** 2 * np.sum(np.abs(Rt[1:] - Rt[:-1]) ** 2)
+        elif interbin == 2:
+            odd = np.sum(np.abs(template_response(z, np.arange(-h, h, dtype=np.float64) + 0.5)) ** 2)
+        else:
+            odd = full
+        out[k] = (full, odd)
+    return out
 
 
 def plane_points(A, zs, zi, col, interbin: bool = True) -> np.ndarray:

@@ -19,6 +19,7 @@ __all__ = [
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
     "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16", "fdas_harmonic_sum",
+    "fdas_noise_means",
     "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
@@ -117,6 +118,7 @@ def load_library():
                                                   c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_harmonic_sum": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_i64, c_i32,
                                              c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
+        "fdas_noise_means": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
         "fdas_batch_plan": (c_i64, [P(fdas_params), P(fdas_trial), c_i32]),
@@ -277,6 +279,11 @@ def fdas_harmonic_sum(p: fdas_params, plane_type: int, plane, width: int, row_st
                                             int(width), int(row_stride), len(thresholds), thr,
                                             _ptr(out), int(cap), _ptr(count), _ptr(status),
                                             _stream(stream)), "fdas_harmonic_sum")
+
+
+def fdas_noise_means(p: fdas_params, means, stream=None) -> None:
+    _check(load_library().fdas_noise_means(ctypes.byref(p), _ptr(means), _stream(stream)),
+           "fdas_noise_means")
 
 
 def fdas_correlate_split(p: fdas_params, prec: int, spec, nb: int, bank, plane, row_stride: int,

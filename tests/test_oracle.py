@@ -411,3 +411,28 @@ def test_harmonic_sum_of_noise_adds_the_mean_powers():
     s = S2[2, 0::2]
     s = s[~np.isnan(s)]
     assert abs(s.mean() - 2 * m_full) < 0.03 * 2 * m_full
+
+
+# ---------------------------------------------------------------- significance
+def test_noise_means_closed_forms_at_z0():
+    m1 = O.noise_means([0.0], 1)[0]
+    assert abs(m1[0] - 1.0) < 1e-15                      # R(0) = 1, R(d != 0) = 0
+    assert abs(m1[1] - 2 * (np.pi / 4) ** 2) < 1e-15     # |R(0) - R(-1)|^2 + |R(1) - R(0)|^2
+    m2 = O.noise_means([0.0], 2)[0]
+    d = np.arange(-8, 8) + 0.5
+    assert abs(m2[1] - np.sum(np.sinc(d) ** 2)) < 1e-14
+
+
+@pytest.mark.parametrize("interbin", [1, 2])
+def test_noise_planes_are_exponential_with_the_predicted_means(interbin):
+    x = synth.make_series(1 << 17, (), 70 + interbin)
+    A = O.normalise(O.real_spectrum(x), 1024)
+    zs = O.z_grid(-30, 30, 15)
+    P = O.plane(A, zs) if interbin == 1 else O.plane_interp2(A, zs)
+    mu = O.noise_means(zs, interbin)
+    for k in range(len(zs)):
+        for e in (0, 1):
+            v = P[k, e::2]
+            assert abs(v.mean() / mu[k, e] - 1.0) < 0.03, (k, e, v.mean(), mu[k, e])
+            tail = np.mean(v / mu[k, e] > 3.0)
+            assert abs(tail - np.exp(-3.0)) < 0.006
