@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched / refinement / split-precision measurements")
     ap.add_argument("--batch-trials", type=int, default=256)
+    ap.add_argument("--rows", default="a9,f1,f2,f3,f4,a11,a10",
+                    help="scope rows measured after the timed steps (comma list)")
     ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2],
                     help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo")
     return ap.parse_args()
@@ -726,15 +728,20 @@ def run_native(args):
             "clocks": clocks,
         }
         if ws == 1 and not args.no_rows:
-            line["rows"] = {"a9_split": split_row(args, torch, dev, S, wl)}
-            line["rows"]["f1_plane16"] = plane16_row(args, torch, dev, S, wl)
-            line["rows"]["f2_interp2"] = interp2_row(args, torch, dev, S, wl)
-            line["rows"]["f3_harmonic"] = harmonic_row(args, torch, dev, S, wl)
-            line["rows"]["f4_significance"] = significance_row(args, torch, dev, S, wl)
-            line["rows"]["a11_refine"] = refine_row(args, torch, dev, S, wl)
+            want = set(args.rows.split(","))
+            rows = {}
+            for key, name, fn in (("a9", "a9_split", split_row), ("f1", "f1_plane16", plane16_row),
+                                  ("f2", "f2_interp2", interp2_row),
+                                  ("f3", "f3_harmonic", harmonic_row),
+                                  ("f4", "f4_significance", significance_row),
+                                  ("a11", "a11_refine", refine_row)):   # a11 last: reuses S
+                if key in want:
+                    rows[name] = fn(args, torch, dev, S, wl)
             del S
             torch.cuda.empty_cache()
-            line["rows"]["a10_batched"] = batched_row(args, torch, dev)
+            if "a10" in want:
+                rows["a10_batched"] = batched_row(args, torch, dev)
+            line["rows"] = rows
         if ws == 1 and not args.no_cpu_baseline:
             v, info = oracle_rate(wl, x, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": info["cores"],
