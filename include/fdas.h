@@ -261,7 +261,7 @@ int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const fl
  * plane: (device) K rows of row_stride 16-bit elements, 16-byte aligned;
  *   row_stride >= fdas_plane_width and a multiple of 4.
  * Other arguments, layout and errors as fdas_correlate; FDAS_E_INVAL for any
- * other type.
+ * other type; FDAS_E_UNSUPPORTED with interbin 2.
  */
 int fdas_correlate_plane16(const fdas_params *p, int32_t type, const float *spec, int64_t nb,
                            const float *bank, void *plane, int64_t row_stride,

@@ -233,6 +233,7 @@ int fdas_correlate_plane16(const fdas_params* p, int32_t type, const float* spec
     int rc = check_correlate(p, &g, spec, nb, bank, static_cast<const float*>(plane), row_stride,
                              fused, status);
     if (rc != FDAS_OK) return rc;
+    if (p->interbin == 2) return FDAS_E_UNSUPPORTED;
     return launch_correlate_plane16(p, g, type, reinterpret_cast<const float2*>(spec), nb,
                                     reinterpret_cast<const float4*>(bank), plane, row_stride,
                                     fused, status, (cudaStream_t)stream);

@@ -29,6 +29,10 @@
 // (Section 4.2): in D3, -k of (thread t, reg i) lives in (partner(t), 15-i)
 // except for thread 0, handled separately.
 //
+// SUB = 2 samples the correlation at every half bin (2-bin Fourier
+// interpolation): the segments are cut from the spectrum with zeros
+// interleaved, 2 nb positions, and the bank holds half-bin templates.
+// OUT selects the plane element type (0 float, 1 binary16, 2 bfloat16).
 // PREC selects the arithmetic of the four radix-16 passes: 0 = FP32 on the
 // CUDA cores; 1, 2 = split-precision tensor-core products (split_mma.cuh,
 // FP16 or BF16 hi+lo operands, FP32 accumulation).  The radix-Q passes, the
@@ -185,7 +189,6 @@ __device__ __forceinline__ float4 pair_powers(float4 x01, float2 xn) {
 struct SeriesState {
     const float2* spec;
     int64_t nb;
-    int64_t np;    // correlation positions: nb, or 2 nb with half-bin sampling
     float* plane;
     int64_t row_stride;
     int64_t end;   // first item of the next series
@@ -199,7 +202,6 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
         const fdas_trial& tr = A.trials[trial];
         st.spec = reinterpret_cast<const float2*>(tr.spec);
         st.nb = tr.nb;
-        st.np = A.interbin == 2 ? 2 * tr.nb : tr.nb;
         st.plane = tr.plane;
         st.row_stride = tr.row_stride;
         st.end = (trial + 1 < A.ntrials) ? A.trials[trial + 1].item_begin : A.items;
@@ -207,7 +209,6 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
     } else {
         st.spec = A.spec;
         st.nb = A.nb;
-        st.np = A.interbin == 2 ? 2 * A.nb : A.nb;
         st.plane = A.plane;
         st.row_stride = A.row_stride;
         st.end = A.items;
@@ -216,7 +217,7 @@ __device__ __forceinline__ SeriesState series_of(const ConvArgs& A, int trial) {
     return st;
 }
 
-template <int L, bool FUSE, bool BATCH, int PREC, int OUT>
+template <int L, bool FUSE, bool BATCH, int PREC, int OUT, int SUB>
 __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const ConvArgs A) {
     using S = ConvShape<L>;
     constexpr int T = S::T, Q = S::Q, G = S::G, BUFS = S::BUFS, NS = S::NS;
@@ -246,15 +247,18 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         trial = a0;
     }
     SeriesState st = series_of<BATCH>(A, trial);
+    // correlation positions of the series: its bins, or twice as many with
+    // half-bin sampling (SUB = 2: the spectrum with zeros interleaved)
+    auto npos = [&]() -> int64_t { return SUB * st.nb; };
     const int64_t first = BATCH ? A.trials[trial].item_begin : 0;
     // group, segment and template of the first item
     int grp = 0;
     int64_t rel = lo - first;
-    int64_t gseg = group_segments(A, L, 0, st.np);
+    int64_t gseg = group_segments(A, L, 0, npos());
     while (rel >= gseg * A.gK[grp] && grp + 1 < A.ng) {
         rel -= gseg * A.gK[grp];
         ++grp;
-        gseg = group_segments(A, L, grp, st.np);
+        gseg = group_segments(A, L, grp, npos());
     }
     M = A.gM[grp];
     B = L - M;
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 s = 0;
                 q = 0;
                 grp = 0;
-                gseg = group_segments(A, L, 0, st.np);
+                gseg = group_segments(A, L, 0, npos());
                 M = A.gM[0];
                 B = L - M;
                 NP = B / 2;
@@ -342,11 +346,11 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int64_t pos = base + i * T + t;
-                    if (A.interbin != 2) {
+                    if constexpr (SUB == 1) {
                         v[i] = (pos >= 0 && pos < st.nb) ? __ldg(&st.spec[pos]) : make_float2(0.f, 0.f);
                     } else {   // the spectrum with zeros interleaved (2-bin interpolation)
-                        v[i] = (pos >= 0 && pos < st.np && !(pos & 1)) ? __ldg(&st.spec[pos >> 1])
-                                                                       : make_float2(0.f, 0.f);
+                        v[i] = (pos >= 0 && pos < npos() && !(pos & 1)) ? __ldg(&st.spec[pos >> 1])
+                                                                          : make_float2(0.f, 0.f);
                     }
                 }
                 forward_fft_d3<L>(v, buf0, buf1, t);
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         const float4* o4 = reinterpret_cast<const float4*>(outb + M / 2);
         const float2* o2 = outb + M / 2 + 2;
         float mx = 0.f;
-        if (r0 + B < st.np) {
+        if (r0 + B < npos()) {
             constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
             if (A.interbin == 1) {
 #pragma unroll
@@ -518,21 +522,21 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
             // segment reaching the end of the spectrum: per-bin checks
             for (int p = t; p < NP; p += T) {
                 const int64_t r = r0 + 2 * p;
-                if (r >= st.np) break;
+                if (r >= npos()) break;
                 float4 pw = pair_powers(o4[p], o2[2 * p]);
-                if (r + 1 >= st.np - 1) pw.w = 0.f;       // no bin r+2
-                if (r >= st.np - 1) pw.y = 0.f;           // no bin r+1
-                if (r + 1 >= st.np) { pw.z = 0.f; pw.w = 0.f; }
+                if (r + 1 >= npos() - 1) pw.w = 0.f;       // no bin r+2
+                if (r >= npos() - 1) pw.y = 0.f;           // no bin r+1
+                if (r + 1 >= npos()) { pw.z = 0.f; pw.w = 0.f; }
                 if (A.interbin == 1) {
                     plane_store1<OUT>(prow, 2 * r, pw.x);
                     plane_store1<OUT>(prow, 2 * r + 1, pw.y);
-                    if (r + 1 < st.np) {
+                    if (r + 1 < npos()) {
                         plane_store1<OUT>(prow, 2 * r + 2, pw.z);
                         plane_store1<OUT>(prow, 2 * r + 3, pw.w);
                     }
                 } else {
                     plane_store1<OUT>(prow, r, pw.x);
-                    if (r + 1 < st.np) plane_store1<OUT>(prow, r + 1, pw.z);
+                    if (r + 1 < npos()) plane_store1<OUT>(prow, r + 1, pw.z);
                     pw.y = 0.f;
                     pw.w = 0.f;
                 }
@@ -544,11 +548,11 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
                 // rare: rescan this thread's pairs and emit each crossing
                 for (int p = t; p < NP; p += T) {
                     const int64_t r = r0 + 2 * p;
-                    if (r >= st.np) break;
+                    if (r >= npos()) break;
                     float4 pw = pair_powers(o4[p], o2[2 * p]);
-                    if (r + 1 >= st.np - 1) pw.w = 0.f;
-                    if (r >= st.np - 1) pw.y = 0.f;
-                    if (r + 1 >= st.np) { pw.z = 0.f; pw.w = 0.f; }
+                    if (r + 1 >= npos() - 1) pw.w = 0.f;
+                    if (r >= npos() - 1) pw.y = 0.f;
+                    if (r + 1 >= npos()) { pw.z = 0.f; pw.w = 0.f; }
                     if (A.interbin == 1) {
                         if (pw.x > A.thr) emit(A, row, 2 * r, pw.x, st.flags);
                         if (pw.y > A.thr) emit(A, row, 2 * r + 1, pw.y, st.flags);
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         q = q_next;
         if (grp_next != grp) {
             grp = grp_next;
-            gseg = group_segments(A, L, grp, st.np);
+            gseg = group_segments(A, L, grp, npos());
             M = A.gM[grp];
             B = L - M;
             NP = B / 2;
@@ -577,13 +581,13 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
     }
 }
 
-template <int L, bool FUSE, bool BATCH, int PREC = 0, int OUT = 0>
+template <int L, bool FUSE, bool BATCH, int PREC = 0, int OUT = 0, int SUB = 1>
 static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     using S = ConvShape<L>;
     constexpr size_t smem = ConvSmem<L>::bytes;
     static int sms = 0, max_per_sm = 0;
     if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH, PREC, OUT>,
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return FDAS_E_CUDA;
@@ -591,7 +595,7 @@ static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
         if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH, PREC, OUT>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB>,
                                                           S::T, smem) != cudaSuccess)
             return FDAS_E_CUDA;
         if (per_sm < 1) return FDAS_E_UNSUPPORTED;
@@ -600,7 +604,7 @@ static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     }
     const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
     const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
-    conv_kernel<L, FUSE, BATCH, PREC, OUT><<<(unsigned)g, S::T, smem, st>>>(args);
+    conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB><<<(unsigned)g, S::T, smem, st>>>(args);
     return cuda_status(cudaGetLastError());
 }
 

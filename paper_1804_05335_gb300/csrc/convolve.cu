@@ -7,6 +7,7 @@ namespace fdas {
 template <bool BATCH>
 static int dispatch(const fdas_params* p, const ConvArgs& a, bool fused, int ctas_per_sm,
                     cudaStream_t st) {
+    if (p->interbin == 2) return dispatch_half_bins(p, a, fused, BATCH, ctas_per_sm, st);
     switch (p->L) {
         case 1024:
             return fused ? launch_one<1024, true, BATCH>(a, ctas_per_sm, st)

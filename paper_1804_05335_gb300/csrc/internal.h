@@ -49,6 +49,10 @@ int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_tri
                              int32_t ntrials, int64_t total_items, const float4* bank,
                              const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
                              cudaStream_t st);
+struct ConvArgs;
+// The convolver with half-bin sampling (interbin 2), convolve_interp2.cu.
+int dispatch_half_bins(const fdas_params* p, const ConvArgs& a, bool fused, bool batch,
+                       int ctas_per_sm, cudaStream_t st);
 int launch_correlate_plane16(const fdas_params* p, const Grid& g, int type, const float2* spec,
                              int64_t nb, const float4* bank, void* plane, int64_t row_stride,
                              const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st);

@@ -166,6 +166,9 @@ def test_interp2_grid_and_split_rejection():
     with pytest.raises(F.FdasError) as e:
         F.fdas_correlate_split(p, 1, 256, 1000, 256, 256, 2000, stream=0)
     assert e.value.code == F.FDAS_E_UNSUPPORTED
+    with pytest.raises(F.FdasError) as e:                # no 16-bit plane at half bins
+        F.fdas_correlate_plane16(p, 1, 256, 1000, 256, 256, 2000, stream=0)
+    assert e.value.code == F.FDAS_E_UNSUPPORTED
 
 
 def test_harmonic_sum_rejects_bad_arguments_before_launch():
