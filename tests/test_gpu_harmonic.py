@@ -44,11 +44,15 @@ def _compare(a, ref, thr):
         assert abs(got[key] - exp[key]) <= 1e-5 * exp[key], key
 
 
-@pytest.mark.parametrize("ptype", [0, 1, 2], ids=["f32", "f16", "bf16"])
-def test_harmonic_sum_matches_oracle_on_random_plane(F, ptype):
+# Row strides with rows on and off 16-byte boundaries.
+@pytest.mark.parametrize("ptype,stride", [(0, 20002), (0, 20004), (1, 20004), (1, 20008),
+                                          (2, 20004), (2, 20008)],
+                         ids=["f32-odd", "f32-aligned", "f16-odd", "f16-aligned", "bf16-odd",
+                              "bf16-aligned"])
+def test_harmonic_sum_matches_oracle_on_random_plane(F, ptype, stride):
     p = F.params(2048, 256, -40, 40, 2, 1)
     K = F.fdas_num_templates(p)
-    width, stride = 20002, 20004
+    width = 20002
     rng = np.random.default_rng(60 + ptype)
     P = rng.exponential(1.0, (K, width)).astype(np.float32)
     P[20, 300] = P[30, 600] = 25.0          # a planted fundamental (z = 0, col 300) at H = 2
@@ -88,3 +92,32 @@ def test_harmonic_sum_overflow_keeps_the_count(F):
     P = torch.full((K, 4000), 10.0, dtype=torch.float32, device="cuda")
     a, k, st = _run(F, p, P, 0, 4000, 4000, [5.0], cap=16)
     assert k > 16 and len(a) == 16 and (st & 2)
+
+
+@pytest.mark.parametrize("zmin,zmax,zstep,width,ptype", [
+    (-40, 40, 2, 4002, 0),      # symmetric grid with a z = 0 row
+    (-10, 50, 2, 4001, 0),      # asymmetric grid, odd width
+    (10, 100, 2, 3000, 1),      # no z = 0 row, 16-bit plane
+    (-200, 200, 1, 3001, 0),    # 401 rows at zstep 1
+    (-200, 200, 1, 3001, 2),    # the same, bfloat16
+    (-600, 600, 1, 1000, 0),    # 1201 rows
+])
+def test_harmonic_sum_lists_every_fundamental_once(F, zmin, zmax, zstep, width, ptype):
+    """With thresholds below every sum, each (fundamental, level) is listed
+    exactly once, with the oracle's sum."""
+    p = F.params(4096, 1024, zmin, zmax, zstep, 1)
+    K = F.fdas_num_templates(p)
+    stride = (width + 7) // 8 * 8
+    rng = np.random.default_rng(K + width)
+    P = rng.exponential(1.0, (K, width)).astype(np.float32)
+    dt = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}[ptype]
+    dev = torch.zeros((K, stride), dtype=dt, device="cuda")
+    dev[:, :width] = torch.from_numpy(P).to(dt)
+    Pq = dev[:, :width].float().cpu().numpy().astype(np.float64)
+    thr = [-1.0, -1.0, -1.0]
+    ref = O.harmonic_candidates(Pq, zmin, zstep, thr)
+    a, k, st = _run(F, p, dev, ptype, width, stride, thr, cap=len(ref[0]) + 16)
+    assert st == 0 and k == len(a) == len(ref[0])
+    keys = {(int(h), int(r), int(c)) for r, c, v, h in a}
+    assert len(keys) == k                                   # no fundamental twice
+    _compare(a, ref, thr)
