@@ -1,6 +1,10 @@
 // Argument validation, grid bookkeeping and the small C-ABI helpers.
 #include <stdlib.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "internal.h"
 
 namespace fdas {
@@ -79,6 +83,27 @@ static void plan_groups(const fdas_params* p, Grid* g) {
         g->gK[k] = rows(ends[k], ends[k + 1]);
         g->gM[k] = rm[ends[k + 1] - 1];
     }
+}
+
+int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, std::pair<int, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find({fn, dev});
+    if (it == done.end()) {
+        int n = 0, per = 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess)
+            return FDAS_E_CUDA;
+        it = done.emplace(std::make_pair(fn, dev), std::make_pair(n, per)).first;
+    }
+    if (sms) *sms = it->second.first;
+    if (per_sm) *per_sm = it->second.second;
+    return it->second.second >= 1 ? FDAS_OK : FDAS_E_UNSUPPORTED;
 }
 
 int make_grid(const fdas_params* p, Grid* g) {

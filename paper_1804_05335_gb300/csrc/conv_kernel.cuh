@@ -585,23 +585,11 @@ template <int L, bool FUSE, bool BATCH, int PREC = 0, int OUT = 0, int SUB = 1>
 static int launch_one(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     using S = ConvShape<L>;
     constexpr size_t smem = ConvSmem<L>::bytes;
-    static int sms = 0, max_per_sm = 0;
-    if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return FDAS_E_CUDA;
-        int dev = 0, n = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return FDAS_E_CUDA;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return FDAS_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB>,
-                                                          S::T, smem) != cudaSuccess)
-            return FDAS_E_CUDA;
-        if (per_sm < 1) return FDAS_E_UNSUPPORTED;
-        max_per_sm = per_sm;
-        sms = n;
-    }
+    int sms = 0, max_per_sm = 0;
+    const int rc = kernel_setup(reinterpret_cast<const void*>(
+                                    &conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB>),
+                                smem, S::T, &sms, &max_per_sm);
+    if (rc != FDAS_OK) return rc;
     const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
     const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
     conv_kernel<L, FUSE, BATCH, PREC, OUT, SUB><<<(unsigned)g, S::T, smem, st>>>(args);

@@ -291,15 +291,20 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
     const int64_t N12 = (int64_t)N1 * N2;
     const size_t tile_sm = (256 + 2 * 256 * kTilePad) * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(fe_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
-            cudaFuncSetAttribute(fe_pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
-            cudaFuncSetAttribute(fe_pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_sm) ||
-            cudaFuncSetAttribute(fe_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 8192 * (int)(sizeof(float2) + sizeof(uint32_t))))
-            return FDAS_E_CUDA;
-        attr = true;
+    {
+        const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
+        int rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a), tile_sm, kFeThreads,
+                              nullptr, nullptr);
+        if (rc == FDAS_OK)
+            rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b), tile_sm, kFeThreads,
+                              nullptr, nullptr);
+        if (rc == FDAS_OK)
+            rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c), tile_sm, kFeThreads,
+                              nullptr, nullptr);
+        if (rc == FDAS_OK)
+            rc = kernel_setup(reinterpret_cast<const void*>(&fe_post), post_max, kFeThreads,
+                              nullptr, nullptr);
+        if (rc != FDAS_OK) return rc;
     }
     float2* sp = reinterpret_cast<float2*>(spec);
     float2* wk = reinterpret_cast<float2*>(work);

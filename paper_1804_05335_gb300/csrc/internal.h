@@ -40,6 +40,12 @@ inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS
 
 inline bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
+// Once per (kernel, current device), thread-safe: allow `smem` bytes of
+// dynamic shared memory for kernel `fn`, and report the device's SM count and
+// how many CTAs of `threads` threads with that shared memory fit on one SM.
+// FDAS_OK, FDAS_E_CUDA, or FDAS_E_UNSUPPORTED when not even one CTA fits.
+int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm);
+
 // Launchers implemented in the .cu files.
 int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st);
 int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,

@@ -83,13 +83,9 @@ __global__ void __launch_bounds__(L / 16) template_fft_kernel(int zfirst, int zs
 template <int L>
 static int launch_fft(int rows, int zfirst, int zstep, int sub, float2* bank, cudaStream_t st) {
     constexpr size_t sm = 2 * ConvShape<L>::BUFS * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(template_fft_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm) != cudaSuccess)
-            return FDAS_E_CUDA;
-        attr = true;
-    }
+    const int rc = kernel_setup(reinterpret_cast<const void*>(&template_fft_kernel<L>), sm, L / 16,
+                                nullptr, nullptr);
+    if (rc != FDAS_OK) return rc;
     template_fft_kernel<L><<<rows, L / 16, sm, st>>>(zfirst, zstep, sub, bank);
     return cuda_status(cudaGetLastError());
 }
