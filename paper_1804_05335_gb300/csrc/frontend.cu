@@ -29,6 +29,12 @@ namespace fdas {
 constexpr int kFeThreads = 256;
 constexpr int kTilePad = 17;   // tile row stride in float2 (16 lines + 1)
 
+// Shared memory of a pass over lines of R points: R twiddles, then the tile
+// x and its transpose buffer y of R rows each.
+__host__ __device__ constexpr size_t tile_bytes(int R) {
+    return (size_t)(R + 2 * R * kTilePad) * sizeof(float2);
+}
+
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -107,8 +113,8 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict
                                                         int64_t N12, int64_t N) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 256;
-    float2* y = x + 256 * kTilePad;
+    float2* x = tw + N3;
+    float2* y = x + N3 * kTilePad;
     const int64_t m0 = (int64_t)blockIdx.x * 16;
     load_tw(tw, N3);
     for (int idx = threadIdx.x; idx < 16 * N3; idx += blockDim.x) {
@@ -128,8 +134,8 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict
 __global__ void __launch_bounds__(kFeThreads) fe_pass_b(float2* __restrict__ buf, int N1, int N2) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 256;
-    float2* y = x + 256 * kTilePad;
+    float2* x = tw + N2;
+    float2* y = x + N2 * kTilePad;
     const int chunks = N1 / 16;
     const int64_t k3 = blockIdx.x / chunks;
     const int n10 = (blockIdx.x % chunks) * 16;
@@ -156,8 +162,8 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_c(const float2* __restrict
                                                         int N3) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + 256;
-    float2* y = x + 256 * kTilePad;
+    float2* x = tw + N1;
+    float2* y = x + N1 * kTilePad;
     const int chunks = N3 / 16;
     const int64_t k2 = blockIdx.x / chunks;
     const int64_t k30 = (int64_t)(blockIdx.x % chunks) * 16;
@@ -184,9 +190,16 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
     for (int shift = 24; shift >= 0; shift -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t k = keys[i];
-            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        // lanes with the same digit add once (the powers of a block share a
+        // few exponent bytes, so per-lane atomics would serialise)
+        for (int i0 = 0; i0 < len; i0 += blockDim.x) {
+            const int i = i0 + (int)threadIdx.x;
+            const uint32_t k = i < len ? keys[i] : 0u;
+            const bool in = i < len && (k & pmask) == prefix;
+            const uint32_t d = in ? (k >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (in && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+                atomicAdd(&hist[d], (uint32_t)__popc(peers));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -290,7 +303,7 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
     const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
     const int64_t N12 = (int64_t)N1 * N2;
-    const size_t tile_sm = (256 + 2 * 256 * kTilePad) * sizeof(float2);
+    const size_t tile_sm = tile_bytes(256);   // the largest line (attribute)
     {
         const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
         int rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a), tile_sm, kFeThreads,
@@ -308,10 +321,10 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     }
     float2* sp = reinterpret_cast<float2*>(spec);
     float2* wk = reinterpret_cast<float2*>(work);
-    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_sm, st>>>(
+    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(
         reinterpret_cast<const float2*>(series), sp, N3, N12, N);
-    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_sm, st>>>(sp, N1, N2);
-    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_sm, st>>>(sp, wk, N1, N2, N3);
+    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(sp, N1, N2);
+    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(sp, wk, N1, N2, N3);
     const int nblk = (int)((N + median_block - 1) / median_block);
     const size_t post_sm = (size_t)median_block * (sizeof(float2) + sizeof(uint32_t));
     fe_post<<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block);
