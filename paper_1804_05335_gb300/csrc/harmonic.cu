@@ -20,6 +20,7 @@
 namespace fdas {
 
 constexpr int kHarmThreads = 256;
+constexpr int kHarmPer = 4;   // fundamentals per thread
 
 template <int TYPE>
 __device__ __forceinline__ float plane_load(const void* plane, int64_t i) {
@@ -58,40 +59,60 @@ __device__ __forceinline__ void harm_emit(const HarmArgs& A, int row, int64_t co
     }
 }
 
-// grid: x over columns, y over the fundamental rows with a second harmonic.
-// Harmonic rows j_h = h (j + j0h) - j0h are linear in h, so the harmonics up
-// to H are all on the plane when j_H is; each thread issues every load of its
-// levels at once and then forms the running sums.
+// One CTA: fundamentals c = blk * kHarmBlock + threadIdx.x + f * kHarmThreads
+// (f < kHarmPer) of fundamental row j.  Each thread issues every load of all
+// its fundamentals before forming the sums.  Harmonic rows j_h = h (j + j0h)
+// - j0h are linear in h, so the harmonics up to H are all on the plane when
+// j_H is.
+constexpr int kHarmBlock = kHarmThreads * kHarmPer;
+
 template <int TYPE>
-__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo) {
-    const int64_t c = (int64_t)blockIdx.x * kHarmThreads + threadIdx.x;
-    const int j = jlo + (int)blockIdx.y;
-    if (2 * c >= A.width) return;
-    int nl = 0;   // levels whose harmonic rows and columns are on the plane
+__device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk) {
+    int nlr = 0;   // levels whose harmonic rows are on the plane
     for (int lev = 0; lev < A.nlev; ++lev) {
         const int H = 2 << lev;
         const int jH = (H - 1) * A.j0h + H * j;
-        if (jH < 0 || jH >= A.K || (int64_t)H * c >= A.width) break;
-        nl = lev + 1;
+        if (jH < 0 || jH >= A.K) break;
+        nlr = lev + 1;
     }
-    float v[8];
+    int64_t rowoff[8];
 #pragma unroll
-    for (int h = 1; h <= 8; ++h) {
-        const int need = h <= 2 ? 1 : (h <= 4 ? 2 : 3);
-        v[h - 1] = 0.f;
-        if (need <= nl) {
-            const int jh = (h - 1) * A.j0h + h * j;
-            v[h - 1] = plane_load<TYPE>(A.plane, (int64_t)jh * A.row_stride + (int64_t)h * c);
+    for (int h = 1; h <= 8; ++h) rowoff[h - 1] = (int64_t)((h - 1) * A.j0h + h * j) * A.row_stride;
+    float v[kHarmPer][8];
+    int nl[kHarmPer];
+    const int64_t c0 = blk * kHarmBlock + threadIdx.x;
+#pragma unroll
+    for (int f = 0; f < kHarmPer; ++f) {
+        const int64_t c = c0 + f * kHarmThreads;
+        int n = 0;   // levels whose columns are on the plane too
+        while (n < nlr && ((int64_t)2 << n) * c < A.width) ++n;
+        nl[f] = n;
+#pragma unroll
+        for (int h = 1; h <= 8; ++h) {
+            const int need = h <= 2 ? 1 : (h <= 4 ? 2 : 3);
+            v[f][h - 1] = 0.f;
+            if (need <= n) v[f][h - 1] = plane_load<TYPE>(A.plane, rowoff[h - 1] + (int64_t)h * c);
         }
     }
-    float s = v[0] + v[1];
-    if (s > A.thr[0]) harm_emit(A, j, c, s, 2);
-    if (nl < 2) return;
-    s += v[2] + v[3];
-    if (s > A.thr[1]) harm_emit(A, j, c, s, 4);
-    if (nl < 3) return;
-    s += (v[4] + v[5]) + (v[6] + v[7]);
-    if (s > A.thr[2]) harm_emit(A, j, c, s, 8);
+#pragma unroll
+    for (int f = 0; f < kHarmPer; ++f) {
+        if (nl[f] == 0) continue;
+        const int64_t c = c0 + f * kHarmThreads;
+        float s = v[f][0] + v[f][1];
+        if (s > A.thr[0]) harm_emit(A, j, c, s, 2);
+        if (nl[f] < 2) continue;
+        s += v[f][2] + v[f][3];
+        if (s > A.thr[1]) harm_emit(A, j, c, s, 4);
+        if (nl[f] < 3) continue;
+        s += (v[f][4] + v[f][5]) + (v[f][6] + v[f][7]);
+        if (s > A.thr[2]) harm_emit(A, j, c, s, 8);
+    }
+}
+
+// Row-major order: x over column blocks, y over the fundamental rows.
+template <int TYPE>
+__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo) {
+    harm_block<TYPE>(A, jlo + (int)blockIdx.y, (int64_t)blockIdx.x);
 }
 
 }  // namespace fdas
@@ -106,7 +127,8 @@ extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const
     int rc = make_grid(p, &g);
     if (rc != FDAS_OK) return rc;
     if (plane_type < 0 || plane_type > 2 || !plane || !thr || !out || !count) return FDAS_E_INVAL;
-    if (nlevels < 1 || nlevels > 3 || width < 1 || row_stride < width || cap < 0)
+    if (nlevels < 1 || nlevels > 3 || width < 1 || width > INT32_MAX || row_stride < width ||
+        cap < 0)
         return FDAS_E_INVAL;
     if (p->zmin % p->zstep != 0) return FDAS_E_INVAL;   // harmonic rows must be grid rows
     if (!aligned(plane, plane_type == 0 ? 4 : 2) || !aligned(out, 4) || !aligned(count, 4))
@@ -137,7 +159,7 @@ extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const
     if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
     if (jhi < 0) return FDAS_OK;
     const int64_t nc = (width + 1) / 2;
-    const dim3 grid((unsigned)((nc + kHarmThreads - 1) / kHarmThreads), (unsigned)(jhi - jlo + 1));
+    const dim3 grid((unsigned)((nc + kHarmBlock - 1) / kHarmBlock), (unsigned)(jhi - jlo + 1));
     switch (plane_type) {
         case 0: harmonic_kernel<0><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
         case 1: harmonic_kernel<1><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;

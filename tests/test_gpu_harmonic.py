@@ -101,6 +101,9 @@ def test_harmonic_sum_overflow_keeps_the_count(F):
     (-200, 200, 1, 3001, 0),    # 401 rows at zstep 1
     (-200, 200, 1, 3001, 2),    # the same, bfloat16
     (-600, 600, 1, 1000, 0),    # 1201 rows
+    (-40, 40, 2, 60002, 0),     # many column blocks per row
+    (-10, 50, 2, 60001, 1),     # the same, asymmetric grid, binary16
+    (10, 100, 2, 120000, 2),    # the same without a z = 0 row, bfloat16
 ])
 def test_harmonic_sum_lists_every_fundamental_once(F, zmin, zmax, zstep, width, ptype):
     """With thresholds below every sum, each (fundamental, level) is listed
