@@ -25,38 +25,50 @@ __device__ __forceinline__ bool is_peak(const float* __restrict__ plane, int row
     return true;
 }
 
+// Each thread takes kThrVec groups of 4 columns, kThrThreads groups apart, and
+// loads all of them before comparing (enough bytes in flight per SM to keep
+// the plane read streaming).
+constexpr int kThrVec = 4;
+
 __global__ void __launch_bounds__(kThrThreads) threshold_kernel(
     const float* __restrict__ plane, int rows, int64_t width, int64_t stride, float thr,
     int want_peak, fdas_cand* __restrict__ out, int cap, int* __restrict__ count,
     int* __restrict__ status, int vec) {
     const int row = blockIdx.y;
-    const int64_t c0 = ((int64_t)blockIdx.x * kThrThreads + threadIdx.x) * 4;
-    if (c0 >= width) return;
     const float* prow = plane + (int64_t)row * stride;
-    float v[4];
-    if (vec && c0 + 3 < width) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(prow + c0));
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
+    float v[kThrVec][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = (c0 + e < width) ? __ldg(prow + c0 + e) : thr;
+    for (int g = 0; g < kThrVec; ++g) {
+        const int64_t c0 = (((int64_t)blockIdx.x * kThrVec + g) * kThrThreads + threadIdx.x) * 4;
+        if (vec && c0 + 3 < width) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(prow + c0));
+            v[g][0] = q.x; v[g][1] = q.y; v[g][2] = q.z; v[g][3] = q.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[g][e] = (c0 + e < width) ? __ldg(prow + c0 + e) : thr;
+        }
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        if (v[e] > thr) {
-            const int64_t col = c0 + e;
-            int flags = 0;
-            if (want_peak && is_peak(plane, rows, width, stride, row, col, v[e])) flags = FDAS_CAND_PEAK;
-            const int idx = atomicAdd(count, 1);
-            if (idx < cap) {
-                fdas_cand c;
-                c.z_idx = row;
-                c.col = (int32_t)col;
-                c.power = v[e];
-                c.flags = flags;
-                out[idx] = c;
-            } else if (status) {
-                atomicOr(status, FDAS_STATUS_OVERFLOW);
+    for (int g = 0; g < kThrVec; ++g) {
+        const int64_t c0 = (((int64_t)blockIdx.x * kThrVec + g) * kThrThreads + threadIdx.x) * 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (v[g][e] > thr) {
+                const int64_t col = c0 + e;
+                int flags = 0;
+                if (want_peak && is_peak(plane, rows, width, stride, row, col, v[g][e]))
+                    flags = FDAS_CAND_PEAK;
+                const int idx = atomicAdd(count, 1);
+                if (idx < cap) {
+                    fdas_cand c;
+                    c.z_idx = row;
+                    c.col = (int32_t)col;
+                    c.power = v[g][e];
+                    c.flags = flags;
+                    out[idx] = c;
+                } else if (status) {
+                    atomicOr(status, FDAS_STATUS_OVERFLOW);
+                }
             }
         }
     }
@@ -78,7 +90,7 @@ extern "C" int fdas_threshold(const float* plane, int32_t rows, int64_t width, i
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
     const int vec = (aligned(plane, 16) && (row_stride % 4) == 0) ? 1 : 0;
-    const int64_t per_cta = 4 * kThrThreads;
+    const int64_t per_cta = (int64_t)4 * kThrThreads * kThrVec;
     dim3 grid((unsigned)((width + per_cta - 1) / per_cta), (unsigned)rows);
     threshold_kernel<<<grid, kThrThreads, 0, st>>>(plane, rows, width, row_stride, thr,
                                                     want_flags & FDAS_CAND_PEAK, out, cap, count,
