@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched / refinement / split-precision measurements")
     ap.add_argument("--batch-trials", type=int, default=256)
-    ap.add_argument("--rows", default="a9,f1,f2,f3,f4,a11,a10",
+    ap.add_argument("--rows", default="a8,a9,f1,f2,f3,f4,a11,a10",
                     help="scope rows measured after the timed steps (comma list)")
     ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2],
                     help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo")
@@ -431,6 +431,32 @@ def interp2_row(args, torch, dev, S, wl):
                            "mean_by_frequency_offset": byfrac}}
 
 
+def threshold_row(args, torch, dev, S, wl):
+    """The separate threshold pass over the production plane (fdas_threshold,
+    with and without the 8-neighbour peak flag): time, the plane read against
+    the measured HBM peak, and the candidate count (the same as the fused
+    threshold's)."""
+    peak, _ = measured_peak()
+    S.correlate(fused=False)
+    res = {}
+    for name, want in (("plain", False), ("peaks", True)):
+        S.threshold(want_peaks=want)
+        ms = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.threshold(want_peaks=want)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        plane_bytes = S.K * S.width * 4
+        res[name] = {"ms": t, "read_gbs": plane_bytes / (t / 1e3) / 1e9,
+                     "frac_of_peak": plane_bytes / (t / 1e3) / 1e9 / peak,
+                     "candidates": int(S.count.item())}
+    return {"threshold": S.thr, "passes": res}
+
+
 def harmonic_row(args, torch, dev, S, wl):
     """Harmonic sums H = 2, 4, 8 with fused thresholds on the production plane
     (FP32, and binary16 from fdas_correlate_plane16): time, useful bytes read
@@ -730,7 +756,8 @@ def run_native(args):
         if ws == 1 and not args.no_rows:
             want = set(args.rows.split(","))
             rows = {}
-            for key, name, fn in (("a9", "a9_split", split_row), ("f1", "f1_plane16", plane16_row),
+            for key, name, fn in (("a8", "a8_threshold", threshold_row),
+                                  ("a9", "a9_split", split_row), ("f1", "f1_plane16", plane16_row),
                                   ("f2", "f2_interp2", interp2_row),
                                   ("f3", "f3_harmonic", harmonic_row),
                                   ("f4", "f4_significance", significance_row),
