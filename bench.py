@@ -500,8 +500,36 @@ def harmonic_row(args, torch, dev, S, wl):
                      "useful_gbs": useful * esize / (ms / 1e3) / 1e9,
                      "useful_frac_of_peak": useful * esize / (ms / 1e3) / 1e9 / peak,
                      "candidates": {str(H): int((h == H).sum()) for H in (2, 4, 8)}}
-    del plane16
-    return {"thresholds": {"2": thr[0], "4": thr[1], "8": thr[2]}, "planes": res}
+    # the same sums with the blocks in ray order (plan built once per grid and width)
+    from paper_1804_05335_gb300 import (fdas_harmonic_plan, fdas_harmonic_plan_bytes,
+                                        fdas_harmonic_sum_planned)
+    nbytes = fdas_harmonic_plan_bytes(S.p, W)
+    plan = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    fdas_harmonic_plan(S.p, W, plan, nbytes)
+    plan_s = time.perf_counter() - t0
+    for name, ptype, pl, esize in (("f32_planned", 0, S.plane, 4), ("f16_planned", 1, plane16, 2)):
+        def run():
+            fdas_harmonic_sum_planned(S.p, ptype, pl, W, S.row_stride, thr, out, cap, cnt, plan,
+                                      nbytes, S.status)
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        k = min(int(cnt.item()), cap)
+        h = out[: 4 * k].view(k, 4)[:, 3].cpu().numpy()
+        res[name] = {"ms": ms, "useful_bytes": useful * esize,
+                     "useful_gbs": useful * esize / (ms / 1e3) / 1e9,
+                     "useful_frac_of_peak": useful * esize / (ms / 1e3) / 1e9 / peak,
+                     "candidates": {str(H): int((h == H).sum()) for H in (2, 4, 8)}}
+    del plane16, plan
+    return {"thresholds": {"2": thr[0], "4": thr[1], "8": thr[2]}, "planes": res,
+            "plan": {"bytes": nbytes, "build_s": plan_s,
+                     "order": "(row, 1024-column block) sorted by u = column / |z/zstep|"}}
 
 
 def significance_row(args, torch, dev, S, wl):

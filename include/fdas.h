@@ -289,6 +289,33 @@ int fdas_harmonic_sum(const fdas_params *p, int32_t plane_type, const void *plan
                       int32_t cap, int32_t *count, int32_t *status, void *stream);
 
 /*
+ * fdas_harmonic_plan_bytes, fdas_harmonic_plan, fdas_harmonic_sum_planned --
+ * fdas_harmonic_sum with its thread blocks taken in ray order.  With y =
+ * z/zstep, a fundamental (y, c) and all its harmonics (h y, h c) share
+ * u = c/|y|.  The plan lists the (fundamental row, block of 1024 columns)
+ * pairs sorted by u, so the rows that read the same 32-byte sectors of the
+ * plane are read close together in time and L2 serves most repeats.  The
+ * results equal fdas_harmonic_sum's: the same candidates, in another order.
+ * fdas_harmonic_plan_bytes: device bytes of the plan for grid p and plane
+ *   width `width` (0 if p is invalid or the plan would pass 2^31 blocks).
+ * fdas_harmonic_plan: builds the plan on the host and copies it to `plan`
+ *   (device, 16-byte aligned, plan_bytes >= fdas_harmonic_plan_bytes); it
+ *   returns when the copy is done.  A plan serves every plane of the same
+ *   grid and width.
+ * fdas_harmonic_sum_planned: arguments as fdas_harmonic_sum, plus the plan.
+ *   A plan made for another grid or width is detected on the device: no
+ *   candidate is listed and FDAS_STATUS_BADPLAN is set in the status word.
+ * Errors: FDAS_E_INVAL (bad params, pointers or sizes), FDAS_E_CUDA.
+ */
+#define FDAS_STATUS_BADPLAN 4   /* status-word bit: a harmonic plan does not match the call */
+size_t fdas_harmonic_plan_bytes(const fdas_params *p, int64_t width);
+int fdas_harmonic_plan(const fdas_params *p, int64_t width, void *plan, size_t plan_bytes);
+int fdas_harmonic_sum_planned(const fdas_params *p, int32_t plane_type, const void *plane,
+                              int64_t width, int64_t row_stride, int32_t nlevels, const float *thr,
+                              fdas_cand *out, int32_t cap, int32_t *count, int32_t *status,
+                              const void *plan, size_t plan_bytes, void *stream);
+
+/*
  * fdas_noise_means -- mean power of pure noise in every plane row, for
  * significances (the paper leaves the statistics of single-bin, interbinned
  * and Fourier-interpolated powers open, Section 5.2).  With the normalised

@@ -19,6 +19,7 @@ __all__ = [
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
     "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16", "fdas_harmonic_sum",
+    "fdas_harmonic_plan_bytes", "fdas_harmonic_plan", "fdas_harmonic_sum_planned", "FDAS_STATUS_BADPLAN",
     "fdas_noise_means",
     "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
@@ -40,6 +41,7 @@ FDAS_E_TIMEOUT = -4
 FDAS_E_UNSUPPORTED = -5
 FDAS_STATUS_TIMEOUT = 1
 FDAS_STATUS_OVERFLOW = 2
+FDAS_STATUS_BADPLAN = 4
 FDAS_CAND_PEAK = 1
 FDAS_NOALLOC_MAX_N = 1 << 20
 FDAS_MAX_GROUPS = 4
@@ -118,6 +120,11 @@ def load_library():
                                                   c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_harmonic_sum": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_i64, c_i32,
                                              c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
+        "fdas_harmonic_plan_bytes": (c_sz, [P(fdas_params), c_i64]),
+        "fdas_harmonic_plan": (ctypes.c_int, [P(fdas_params), c_i64, c_vp, c_sz]),
+        "fdas_harmonic_sum_planned": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_i64,
+                                                     c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                                                     c_sz, c_vp]),
         "fdas_noise_means": (ctypes.c_int, [P(fdas_params), c_vp, c_vp]),
         "fdas_threshold": (ctypes.c_int, [c_vp, c_i32, c_i64, c_i64, c_f32, c_i32, c_vp, c_i32,
                                           c_vp, c_vp, c_vp]),
@@ -279,6 +286,28 @@ def fdas_harmonic_sum(p: fdas_params, plane_type: int, plane, width: int, row_st
                                             int(width), int(row_stride), len(thresholds), thr,
                                             _ptr(out), int(cap), _ptr(count), _ptr(status),
                                             _stream(stream)), "fdas_harmonic_sum")
+
+
+def fdas_harmonic_plan_bytes(p: fdas_params, width: int) -> int:
+    """Device bytes of the ray-order plan for grid p and plane width (0: invalid)."""
+    return int(load_library().fdas_harmonic_plan_bytes(ctypes.byref(p), int(width)))
+
+
+def fdas_harmonic_plan(p: fdas_params, width: int, plan, plan_bytes: int) -> None:
+    """Build the ray-order plan into device memory `plan` (returns when copied)."""
+    _check(load_library().fdas_harmonic_plan(ctypes.byref(p), int(width), _ptr(plan),
+                                             int(plan_bytes)), "fdas_harmonic_plan")
+
+
+def fdas_harmonic_sum_planned(p: fdas_params, plane_type: int, plane, width: int,
+                              row_stride: int, thresholds, out, cap: int, count, plan,
+                              plan_bytes: int, status=None, stream=None) -> None:
+    """fdas_harmonic_sum with its blocks taken in the plan's ray order."""
+    thr = (c_f32 * 3)(*[float(v) for v in thresholds])
+    _check(load_library().fdas_harmonic_sum_planned(
+        ctypes.byref(p), int(plane_type), _ptr(plane), int(width), int(row_stride),
+        len(thresholds), thr, _ptr(out), int(cap), _ptr(count), _ptr(status), _ptr(plan),
+        int(plan_bytes), _stream(stream)), "fdas_harmonic_sum_planned")
 
 
 def fdas_noise_means(p: fdas_params, means, stream=None) -> None:

@@ -15,6 +15,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "internal.h"
 
 namespace fdas {
@@ -115,14 +119,106 @@ __global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A
     harm_block<TYPE>(A, jlo + (int)blockIdx.y, (int64_t)blockIdx.x);
 }
 
+// Ray-ordered launch: block b takes entry b of a plan, (row j, column block).
+// The plan header holds what it was made for; a mismatch lists nothing.
+constexpr int32_t kPlanMagic = 0x48504c31;   // "HPL1"
+constexpr int kPlanHeaderWords = 16;         // int32 words before the entries (64 bytes)
+
+template <int TYPE>
+__global__ void __launch_bounds__(kHarmThreads) harmonic_planned_kernel(const HarmArgs A,
+                                                                       const int32_t* hdr) {
+    const int64_t width = (int64_t)(uint32_t)hdr[3] | ((int64_t)hdr[4] << 32);
+    if (hdr[0] != kPlanMagic || hdr[1] != A.K || hdr[2] != A.j0h || width != A.width) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && A.status)
+            atomicOr(A.status, FDAS_STATUS_BADPLAN);
+        return;
+    }
+    const int2 e = reinterpret_cast<const int2*>(hdr + kPlanHeaderWords)[blockIdx.x];
+    harm_block<TYPE>(A, e.x, (int64_t)e.y);
+}
+
+// Fundamental rows (second harmonic on the plane) and column blocks of a
+// plan; false for invalid arguments or more than 2^31 - 1 blocks.
+static bool plan_shape(const fdas_params* p, int64_t width, Grid* g, int* jlo, int* jhi,
+                       int64_t* nblk) {
+    if (make_grid(p, g) != FDAS_OK || p->zmin % p->zstep != 0 || width < 1 || width > INT32_MAX)
+        return false;
+    const int j0h = p->zmin / p->zstep;
+    *jlo = 0;
+    *jhi = -1;
+    for (int j = 0; j < g->K; ++j) {
+        const int j2 = j0h + 2 * j;
+        if (j2 >= 0 && j2 < g->K) {
+            if (*jhi < 0) *jlo = j;
+            *jhi = j;
+        }
+    }
+    const int64_t nc = (width + 1) / 2;
+    *nblk = (nc + kHarmBlock - 1) / kHarmBlock;
+    const int64_t rows = *jhi >= *jlo ? *jhi - *jlo + 1 : 0;
+    return rows * *nblk < ((int64_t)1 << 31);
+}
+
 }  // namespace fdas
 
 using namespace fdas;
 
-extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const void* plane,
-                                 int64_t width, int64_t row_stride, int32_t nlevels,
-                                 const float* thr, fdas_cand* out, int32_t cap, int32_t* count,
-                                 int32_t* status, void* stream) {
+extern "C" size_t fdas_harmonic_plan_bytes(const fdas_params* p, int64_t width) {
+    Grid g;
+    int jlo, jhi;
+    int64_t nblk;
+    if (!plan_shape(p, width, &g, &jlo, &jhi, &nblk)) return 0;
+    const int64_t n = (jhi >= jlo ? jhi - jlo + 1 : 0) * nblk;
+    return (size_t)(4 * kPlanHeaderWords + 8 * n + 15) / 16 * 16;
+}
+
+extern "C" int fdas_harmonic_plan(const fdas_params* p, int64_t width, void* plan,
+                                  size_t plan_bytes) {
+    Grid g;
+    int jlo, jhi;
+    int64_t nblk;
+    if (!plan_shape(p, width, &g, &jlo, &jhi, &nblk)) return FDAS_E_INVAL;
+    if (!plan || !aligned(plan, 16) || plan_bytes < fdas_harmonic_plan_bytes(p, width))
+        return FDAS_E_INVAL;
+    const int j0h = p->zmin / p->zstep;
+    const int64_t rows = jhi >= jlo ? jhi - jlo + 1 : 0;
+    std::vector<std::pair<double, int64_t>> key((size_t)(rows * nblk));
+    size_t i = 0;
+    for (int j = jlo; j <= jhi; ++j) {
+        const int ay = std::abs(j + j0h);
+        for (int64_t b = 0; b < nblk; ++b, ++i) {
+            // u of the block's middle; the z = 0 row (no u) first, in column order
+            const double u = ay ? (b + 0.5) / ay : -1.0 + (double)b / (double)nblk;
+            key[i] = {u, (int64_t)j * nblk + b};
+        }
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
+                         return x.first < y.first;
+                     });
+    std::vector<int32_t> host((size_t)(kPlanHeaderWords + 2 * key.size()), 0);
+    host[0] = kPlanMagic;
+    host[1] = g.K;
+    host[2] = j0h;
+    host[3] = (int32_t)(uint32_t)(width & 0xffffffff);
+    host[4] = (int32_t)(width >> 32);
+    host[5] = (int32_t)key.size();
+    for (size_t e = 0; e < key.size(); ++e) {
+        host[kPlanHeaderWords + 2 * e] = (int32_t)(key[e].second / nblk);
+        host[kPlanHeaderWords + 2 * e + 1] = (int32_t)(key[e].second % nblk);
+    }
+    return cuda_status(cudaMemcpy(plan, host.data(), host.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice));
+}
+
+namespace fdas {
+
+// Checks shared by both harmonic-sum entries; fills the kernel arguments and
+// the range of fundamental rows [jlo, jhi] (jhi < jlo: none).
+static int harmonic_args(const fdas_params* p, int32_t plane_type, const void* plane,
+                         int64_t width, int64_t row_stride, int32_t nlevels, const float* thr,
+                         fdas_cand* out, int32_t cap, int32_t* count, int32_t* status,
+                         HarmArgs* a, int* jlo, int* jhi) {
     Grid g;
     int rc = make_grid(p, &g);
     if (rc != FDAS_OK) return rc;
@@ -134,27 +230,41 @@ extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const
     if (!aligned(plane, plane_type == 0 ? 4 : 2) || !aligned(out, 4) || !aligned(count, 4))
         return FDAS_E_INVAL;
     if (status && !aligned(status, 4)) return FDAS_E_INVAL;
-    HarmArgs a;
-    a.plane = plane;
-    a.width = width;
-    a.row_stride = row_stride;
-    a.K = g.K;
-    a.j0h = p->zmin / p->zstep;
-    a.nlev = nlevels;
-    for (int l = 0; l < 3; ++l) a.thr[l] = l < nlevels ? thr[l] : 0.f;
-    a.out = out;
-    a.cap = cap;
-    a.count = count;
-    a.status = status;
+    a->plane = plane;
+    a->width = width;
+    a->row_stride = row_stride;
+    a->K = g.K;
+    a->j0h = p->zmin / p->zstep;
+    a->nlev = nlevels;
+    for (int l = 0; l < 3; ++l) a->thr[l] = l < nlevels ? thr[l] : 0.f;
+    a->out = out;
+    a->cap = cap;
+    a->count = count;
+    a->status = status;
     // fundamental rows whose second harmonic row 2 j + j0h lies in [0, K)
-    int jlo = 0, jhi = -1;
+    *jlo = 0;
+    *jhi = -1;
     for (int j = 0; j < g.K; ++j) {
-        const int j2 = a.j0h + 2 * j;
+        const int j2 = a->j0h + 2 * j;
         if (j2 >= 0 && j2 < g.K) {
-            if (jhi < 0) jlo = j;
-            jhi = j;
+            if (*jhi < 0) *jlo = j;
+            *jhi = j;
         }
     }
+    return FDAS_OK;
+}
+
+}  // namespace fdas
+
+extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const void* plane,
+                                 int64_t width, int64_t row_stride, int32_t nlevels,
+                                 const float* thr, fdas_cand* out, int32_t cap, int32_t* count,
+                                 int32_t* status, void* stream) {
+    HarmArgs a;
+    int jlo, jhi;
+    const int rc = harmonic_args(p, plane_type, plane, width, row_stride, nlevels, thr, out, cap,
+                                 count, status, &a, &jlo, &jhi);
+    if (rc != FDAS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
     if (jhi < 0) return FDAS_OK;
@@ -164,6 +274,32 @@ extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const
         case 0: harmonic_kernel<0><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
         case 1: harmonic_kernel<1><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
         default: harmonic_kernel<2><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int fdas_harmonic_sum_planned(const fdas_params* p, int32_t plane_type,
+                                         const void* plane, int64_t width, int64_t row_stride,
+                                         int32_t nlevels, const float* thr, fdas_cand* out,
+                                         int32_t cap, int32_t* count, int32_t* status,
+                                         const void* plan, size_t plan_bytes, void* stream) {
+    HarmArgs a;
+    int jlo, jhi;
+    const int rc = harmonic_args(p, plane_type, plane, width, row_stride, nlevels, thr, out, cap,
+                                 count, status, &a, &jlo, &jhi);
+    if (rc != FDAS_OK) return rc;
+    const size_t need = fdas_harmonic_plan_bytes(p, width);
+    if (need == 0 || !plan || !aligned(plan, 16) || plan_bytes < need) return FDAS_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
+    if (jhi < 0) return FDAS_OK;
+    const int64_t nc = (width + 1) / 2;
+    const int64_t n = (int64_t)(jhi - jlo + 1) * ((nc + kHarmBlock - 1) / kHarmBlock);
+    const int32_t* hdr = static_cast<const int32_t*>(plan);
+    switch (plane_type) {
+        case 0: harmonic_planned_kernel<0><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
+        case 1: harmonic_planned_kernel<1><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
+        default: harmonic_planned_kernel<2><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
     }
     return cuda_status(cudaGetLastError());
 }

@@ -187,3 +187,24 @@ def test_harmonic_sum_rejects_bad_arguments_before_launch():
             f()
         if isinstance(e.value, F.FdasError):
             assert e.value.code == F.FDAS_E_INVAL
+
+
+def test_harmonic_plan_sizes_and_validation():
+    p = F.params(2048, 256, -200, 200, 2, 1)
+    # 101 fundamental rows (second harmonic on the plane) x 4096 blocks of 1024 columns
+    assert F.fdas_harmonic_plan_bytes(p, 1 << 23) == 64 + 8 * 101 * 4096
+    assert F.fdas_harmonic_plan_bytes(p, 1000) == (64 + 8 * 101 + 15) // 16 * 16
+    assert F.fdas_harmonic_plan_bytes(p, 0) == 0
+    bad = F.params(2048, 256, -201, 199, 2, 1)            # zmin not a multiple of zstep
+    assert F.fdas_harmonic_plan_bytes(bad, 1000) == 0
+    need = F.fdas_harmonic_plan_bytes(p, 1000)
+    for args in [(p, 1000, 0, need), (p, 1000, 264, need), (p, 1000, 256, need - 16),
+                 (bad, 1000, 256, need)]:
+        with pytest.raises(F.FdasError) as e:
+            F.fdas_harmonic_plan(*args)
+        assert e.value.code == F.FDAS_E_INVAL
+    for plan, nbytes in [(0, need), (264, need), (256, need - 16)]:   # NULL, unaligned, short
+        with pytest.raises(F.FdasError) as e:
+            F.fdas_harmonic_sum_planned(p, 0, 256, 1000, 1000, [20.0], 256, 4, 256, plan,
+                                        nbytes, stream=0)
+        assert e.value.code == F.FDAS_E_INVAL

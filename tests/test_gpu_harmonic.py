@@ -124,3 +124,52 @@ def test_harmonic_sum_lists_every_fundamental_once(F, zmin, zmax, zstep, width, 
     keys = {(int(h), int(r), int(c)) for r, c, v, h in a}
     assert len(keys) == k                                   # no fundamental twice
     _compare(a, ref, thr)
+
+
+def _planned(F, p, plane_dev, ptype, width, stride, thr, plan, nbytes, cap=1 << 20):
+    out = torch.zeros(4 * cap, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    F.fdas_harmonic_sum_planned(p, ptype, plane_dev, width, stride, thr, out, cap, count, plan,
+                                nbytes, status)
+    k = int(count.item())
+    return out[: 4 * min(k, cap)].view(-1, 4).cpu().numpy(), k, int(status.item())
+
+
+@pytest.mark.parametrize("zmin,zmax,zstep,width,stride,ptype", [
+    (-40, 40, 2, 60002, 60008, 0),      # z = 0 row first, then ray order
+    (-10, 50, 2, 60001, 60008, 1),      # asymmetric grid, binary16
+    (10, 100, 2, 120000, 120000, 2),    # no z = 0 row, bfloat16
+    (-200, 200, 2, 20002, 20004, 0),    # the production grid on a short plane
+])
+def test_planned_harmonic_sum_equals_the_unplanned_one(F, zmin, zmax, zstep, width, stride,
+                                                       ptype):
+    """The ray-ordered launch lists exactly the candidates of the row-major
+    one, with bit-identical sums (same arithmetic, other block order)."""
+    p = F.params(4096, 1024, zmin, zmax, zstep, 1)
+    K = F.fdas_num_templates(p)
+    rng = np.random.default_rng(K + width + ptype)
+    P = rng.exponential(1.0, (K, width)).astype(np.float32)
+    dt = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}[ptype]
+    dev = torch.zeros((K, stride), dtype=dt, device="cuda")
+    dev[:, :width] = torch.from_numpy(P).to(dt)
+    thr = [7.0, 11.0, 17.0]
+    nbytes = F.fdas_harmonic_plan_bytes(p, width)
+    plan = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    F.fdas_harmonic_plan(p, width, plan, nbytes)
+    a, k, st = _run(F, p, dev, ptype, width, stride, thr, cap=1 << 20)
+    b, kb, stb = _planned(F, p, dev, ptype, width, stride, thr, plan, nbytes)
+    assert st == 0 and stb == 0 and k == kb and k > 0
+    key = lambda x: sorted(map(tuple, x.tolist()))
+    assert key(a) == key(b)
+
+
+def test_planned_harmonic_sum_rejects_a_plan_for_another_width(F):
+    p = F.params(2048, 256, -40, 40, 2, 1)
+    K = F.fdas_num_templates(p)
+    dev = torch.full((K, 8000), 10.0, dtype=torch.float32, device="cuda")
+    n1, n2 = F.fdas_harmonic_plan_bytes(p, 4000), F.fdas_harmonic_plan_bytes(p, 8000)
+    plan = torch.empty(max(n1, n2), dtype=torch.uint8, device="cuda")
+    F.fdas_harmonic_plan(p, 4000, plan, n1)
+    b, k, st = _planned(F, p, dev, 0, 8000, 8000, [5.0], plan, max(n1, n2))
+    assert k == 0 and (st & F.FDAS_STATUS_BADPLAN)
