@@ -496,26 +496,39 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
         float mx = 0.f;
         if (r0 + B < npos()) {
             constexpr int UMAX = (L / 2 - 32 + T - 1) / T;   // pairs per thread for M >= 64
+            auto pair_ib = [&](int p) {
+                const float4 pw = pair_powers(o4[p], o2[2 * p]);
+                plane_store4<OUT>(prow, 2 * r0 + 4 * p, pw);
+                if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
+            };
+            auto pair_full = [&](int p) {
+                const float4 x = o4[p];
+                const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
+                plane_store2<OUT>(prow, r0 + 2 * p, pw);
+                if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
+            };
+            // with NP >= (UMAX - 1) T (overlaps up to L - 2 (UMAX - 1) T) only a
+            // thread's last pair can fall past NP
+            const bool head = NP >= (UMAX - 1) * T;
             if (A.interbin == 1) {
+                if (head) {
 #pragma unroll
-                for (int u = 0; u < UMAX; ++u) {
-                    const int p = t + u * T;
-                    if (p < NP) {
-                        const float4 pw = pair_powers(o4[p], o2[2 * p]);
-                        plane_store4<OUT>(prow, 2 * r0 + 4 * p, pw);
-                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(fmaxf(pw.x, pw.y), fmaxf(pw.z, pw.w)));
-                    }
+                    for (int u = 0; u < UMAX - 1; ++u) pair_ib(t + u * T);
+                    if (t + (UMAX - 1) * T < NP) pair_ib(t + (UMAX - 1) * T);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < UMAX; ++u)
+                        if (t + u * T < NP) pair_ib(t + u * T);
                 }
             } else {
+                if (head) {
 #pragma unroll
-                for (int u = 0; u < UMAX; ++u) {
-                    const int p = t + u * T;
-                    if (p < NP) {
-                        const float4 x = o4[p];
-                        const float2 pw = make_float2(fmaf(x.x, x.x, x.y * x.y), fmaf(x.z, x.z, x.w * x.w));
-                        plane_store2<OUT>(prow, r0 + 2 * p, pw);
-                        if constexpr (FUSE) mx = fmaxf(mx, fmaxf(pw.x, pw.y));
-                    }
+                    for (int u = 0; u < UMAX - 1; ++u) pair_full(t + u * T);
+                    if (t + (UMAX - 1) * T < NP) pair_full(t + (UMAX - 1) * T);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < UMAX; ++u)
+                        if (t + u * T < NP) pair_full(t + u * T);
                 }
             }
         } else {
