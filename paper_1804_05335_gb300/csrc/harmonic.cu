@@ -7,11 +7,16 @@
 // r = c/2 (interbinned) or r = c, so harmonic h of (j, c) sits at column h c
 // and at row j_h = (h - 1) zmin / zstep + h j, which is a grid row whenever
 // zmin is a multiple of zstep.  For every fundamental whose second harmonic
-// is on the plane, one thread forms
+// is on the plane a thread forms
 //   S_2 = P[j][c] + P[j_2][2c],  S_4 = S_2 + P[j_3][3c] + P[j_4][4c],
 //   S_8 = S_4 + P[j_5][5c] + ... + P[j_8][8c],
 // stopping at the first level whose harmonics leave the plane, and lists
 // (row j, column c, S_H, H) for every S_H above that level's threshold.
+// A block takes 1024 consecutive fundamentals of one row, four per thread.
+// fdas_harmonic_sum launches the blocks row by row; fdas_harmonic_sum_planned
+// takes them from a plan sorted by u = c / |z/zstep|, the quantity a
+// fundamental shares with all its harmonics, so that the rows reading the
+// same plane sectors run together and L2 serves the repeats.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
