@@ -190,16 +190,9 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
     for (int shift = 24; shift >= 0; shift -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        // lanes with the same digit add once (the powers of a block share a
-        // few exponent bytes, so per-lane atomics would serialise)
-        for (int i0 = 0; i0 < len; i0 += blockDim.x) {
-            const int i = i0 + (int)threadIdx.x;
-            const uint32_t k = i < len ? keys[i] : 0u;
-            const bool in = i < len && (k & pmask) == prefix;
-            const uint32_t d = in ? (k >> shift) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (in && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-                atomicAdd(&hist[d], (uint32_t)__popc(peers));
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t k = keys[i];
+            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
         }
         __syncthreads();
         if (threadIdx.x < 32) {
