@@ -173,3 +173,27 @@ def test_planned_harmonic_sum_rejects_a_plan_for_another_width(F):
     F.fdas_harmonic_plan(p, 4000, plan, n1)
     b, k, st = _planned(F, p, dev, 0, 8000, 8000, [5.0], plan, max(n1, n2))
     assert k == 0 and (st & F.FDAS_STATUS_BADPLAN)
+
+
+@pytest.mark.parametrize("width", [1, 2, 3, 5])
+def test_harmonic_sum_on_degenerate_widths(F, width):
+    """Planes one to five columns wide: every listed sum is the oracle's, and
+    the planned launch lists the same candidates."""
+    p = F.params(2048, 256, -20, 20, 2, 1)
+    K = F.fdas_num_templates(p)
+    rng = np.random.default_rng(width)
+    P = rng.exponential(1.0, (K, width)).astype(np.float32)
+    stride = 8
+    dev = torch.zeros((K, stride), dtype=torch.float32, device="cuda")
+    dev[:, :width] = torch.from_numpy(P)
+    thr = [-1.0, -1.0, -1.0]
+    ref = O.harmonic_candidates(dev[:, :width].cpu().numpy().astype(np.float64), -20, 2, thr)
+    a, k, st = _run(F, p, dev, 0, width, stride, thr)
+    assert st == 0 and k == len(ref[0])
+    _compare(a, ref, thr)
+    nbytes = F.fdas_harmonic_plan_bytes(p, width)
+    plan = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    F.fdas_harmonic_plan(p, width, plan, nbytes)
+    b, kb, stb = _planned(F, p, dev, 0, width, stride, thr, plan, nbytes)
+    assert stb == 0 and kb == k
+    assert sorted(map(tuple, a.tolist())) == sorted(map(tuple, b.tolist()))
