@@ -118,16 +118,25 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
     }
 }
 
-// Row-major order: x over column blocks, y over the fundamental rows.
+// Row-major order: x over groups of kRowPer column blocks, y over the
+// fundamental rows.
+constexpr int kRowPer = 16;
+
 template <int TYPE>
-__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo) {
-    harm_block<TYPE>(A, jlo + (int)blockIdx.y, (int64_t)blockIdx.x);
+__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo,
+                                                                int64_t nblk) {
+    for (int g = 0; g < kRowPer; ++g) {
+        const int64_t blk = (int64_t)blockIdx.x * kRowPer + g;
+        if (blk >= nblk) break;
+        harm_block<TYPE>(A, jlo + (int)blockIdx.y, blk);
+    }
 }
 
 // Ray-ordered launch: block b takes entry b of a plan, (row j, column block).
 // The plan header holds what it was made for; a mismatch lists nothing.
 constexpr int32_t kPlanMagic = 0x48504c31;   // "HPL1"
 constexpr int kPlanHeaderWords = 16;         // int32 words before the entries (64 bytes)
+constexpr int kPlanPer = 8;                  // plan entries per block
 
 template <int TYPE>
 __global__ void __launch_bounds__(kHarmThreads) harmonic_planned_kernel(const HarmArgs A,
@@ -138,8 +147,14 @@ __global__ void __launch_bounds__(kHarmThreads) harmonic_planned_kernel(const Ha
             atomicOr(A.status, FDAS_STATUS_BADPLAN);
         return;
     }
-    const int2 e = reinterpret_cast<const int2*>(hdr + kPlanHeaderWords)[blockIdx.x];
-    harm_block<TYPE>(A, e.x, (int64_t)e.y);
+    const int2* ent = reinterpret_cast<const int2*>(hdr + kPlanHeaderWords);
+    const int n = hdr[5];
+    for (int g = 0; g < kPlanPer; ++g) {
+        const int i = blockIdx.x * kPlanPer + g;
+        if (i >= n) break;
+        const int2 e = ent[i];
+        harm_block<TYPE>(A, e.x, (int64_t)e.y);
+    }
 }
 
 // Fundamental rows (second harmonic on the plane) and column blocks of a
@@ -274,11 +289,12 @@ extern "C" int fdas_harmonic_sum(const fdas_params* p, int32_t plane_type, const
     if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return FDAS_E_CUDA;
     if (jhi < 0) return FDAS_OK;
     const int64_t nc = (width + 1) / 2;
-    const dim3 grid((unsigned)((nc + kHarmBlock - 1) / kHarmBlock), (unsigned)(jhi - jlo + 1));
+    const int64_t nblk = (nc + kHarmBlock - 1) / kHarmBlock;
+    const dim3 grid((unsigned)((nblk + kRowPer - 1) / kRowPer), (unsigned)(jhi - jlo + 1));
     switch (plane_type) {
-        case 0: harmonic_kernel<0><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
-        case 1: harmonic_kernel<1><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
-        default: harmonic_kernel<2><<<grid, kHarmThreads, 0, st>>>(a, jlo); break;
+        case 0: harmonic_kernel<0><<<grid, kHarmThreads, 0, st>>>(a, jlo, nblk); break;
+        case 1: harmonic_kernel<1><<<grid, kHarmThreads, 0, st>>>(a, jlo, nblk); break;
+        default: harmonic_kernel<2><<<grid, kHarmThreads, 0, st>>>(a, jlo, nblk); break;
     }
     return cuda_status(cudaGetLastError());
 }
@@ -301,10 +317,11 @@ extern "C" int fdas_harmonic_sum_planned(const fdas_params* p, int32_t plane_typ
     const int64_t nc = (width + 1) / 2;
     const int64_t n = (int64_t)(jhi - jlo + 1) * ((nc + kHarmBlock - 1) / kHarmBlock);
     const int32_t* hdr = static_cast<const int32_t*>(plan);
+    const int64_t nb = (n + kPlanPer - 1) / kPlanPer;
     switch (plane_type) {
-        case 0: harmonic_planned_kernel<0><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
-        case 1: harmonic_planned_kernel<1><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
-        default: harmonic_planned_kernel<2><<<(unsigned)n, kHarmThreads, 0, st>>>(a, hdr); break;
+        case 0: harmonic_planned_kernel<0><<<(unsigned)nb, kHarmThreads, 0, st>>>(a, hdr); break;
+        case 1: harmonic_planned_kernel<1><<<(unsigned)nb, kHarmThreads, 0, st>>>(a, hdr); break;
+        default: harmonic_planned_kernel<2><<<(unsigned)nb, kHarmThreads, 0, st>>>(a, hdr); break;
     }
     return cuda_status(cudaGetLastError());
 }
