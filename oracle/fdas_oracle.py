@@ -59,7 +59,7 @@ __all__ = [
     "power_plane", "plane", "plane_window", "plane_points", "threshold", "peak_flags",
     "search", "oracle_threads", "PEAK_FLAG", "response_derivs_quadrature", "refine_taps",
     "correlate_half", "plane_interp2", "harmonic_sum", "harmonic_candidates", "noise_means",
-    "refine_power", "refine_grad_spec", "refine_ascent",
+    "refine_power", "refine_grad_spec", "refine_ascent", "exp_sum_log_tail", "sigma_of_log_tail",
 ]
 
 PEAK_FLAG = 1
@@ -376,8 +376,10 @@ def harmonic_sum(P, zmin: int, zstep: int, H: int) -> np.ndarray:
 
 
 def harmonic_candidates(P, zmin: int, zstep: int, thresholds):
-    """(rows, cols, sums, H) with S_H > thresholds[level] for H = 2, 4, 8, for
-    fundamentals whose second harmonic is on the plane; sorted by (H, row, col)."""
+    """(rows, cols, sums, H) with S_H > thresholds[level] (strict) for levels
+    0, 1, 2 -> H = 2, 4, 8, for the fundamentals whose H harmonics all lie on
+    the plane (harmonic_sum is NaN elsewhere and lists nothing); sorted by
+    (H, row, col)."""
     out = []
     for lev, thr in enumerate(thresholds):
         H = 2 << lev
@@ -546,3 +548,56 @@ def refine_ascent(A, r0: float, z0: float, m: int, steps: int = 20, lr_r: float 
         r += min(max(lr_r * gr / P, -0.5), 0.5)
         z += min(max(lr_z * gz / P, -2.0), 2.0)
     return r, z, P
+
+
+# --------------------------------------------------------------------------
+# significance: exact tails of plane powers and their harmonic sums
+# --------------------------------------------------------------------------
+def exp_sum_log_tail(x: float, means, dps: int = 80) -> float:
+    """log P(X_1 + ... + X_H > x) for independent exponential X_i with the
+    given means (noise powers of the H harmonics: Section 5.2 leaves their
+    statistics open; each normalised plane value is exponential).
+
+    By definition, in arbitrary precision (mpmath, `dps` digits):
+      all means equal (m):  the Erlang tail  e^{-x/m} sum_{k<H} (x/m)^k / k!;
+      all means distinct:   the hypoexponential tail
+        sum_i prod_{j != i} m_i / (m_i - m_j) * e^{-x/m_i},
+    which cancels badly in FP64 when the means are close; the precision
+    absorbs that.  Means that repeat only in part are not supported."""
+    import mpmath as mp
+    m = [float(v) for v in np.atleast_1d(means)]
+    if any(v <= 0.0 for v in m):
+        raise ValueError("means must be positive")
+    with mp.workdps(dps):
+        X = mp.mpf(x)
+        if X <= 0:
+            return 0.0
+        if all(v == m[0] for v in m):
+            u = X / mp.mpf(m[0])
+            tail = mp.e ** (-u) * mp.fsum(u ** k / mp.factorial(k) for k in range(len(m)))
+        elif len(set(m)) == len(m):
+            M = [mp.mpf(v) for v in m]
+            tail = mp.mpf(0)
+            for i, mi in enumerate(M):
+                c = mp.mpf(1)
+                for j, mj in enumerate(M):
+                    if j != i:
+                        c *= mi / (mi - mj)
+                tail += c * mp.e ** (-X / mi)
+        else:
+            raise ValueError("means must be all equal or all distinct")
+        return float(mp.log(tail))
+
+
+def sigma_of_log_tail(logp: float, dps: int = 50) -> float:
+    """One-sided Gaussian sigma s with P(N(0,1) > s) = exp(logp), i.e. the root
+    of log(erfc(s / sqrt 2) / 2) = logp, found in arbitrary precision; 0 when
+    exp(logp) >= 1/2."""
+    import mpmath as mp
+    if logp >= math.log(0.5):
+        return 0.0
+    with mp.workdps(dps):
+        lp = mp.mpf(logp)
+        f = lambda s: mp.log(mp.erfc(s / mp.sqrt(2)) / 2) - lp
+        s0 = mp.sqrt(-2 * lp)          # bracket: the root lies in (0, sqrt(-2 logp)]
+        return float(mp.findroot(f, (mp.mpf("1e-30"), s0), solver="illinois"))

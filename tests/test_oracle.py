@@ -413,6 +413,53 @@ def test_harmonic_sum_of_noise_adds_the_mean_powers():
     assert abs(s.mean() - 2 * m_full) < 0.03 * 2 * m_full
 
 
+def _brute_harmonic_candidates(P, zmin, zstep, thresholds):
+    """Independent triple loop over (level, row, column): every fundamental
+    whose H harmonics (h z_j, h c) all fall on the plane, summed, kept if the
+    sum is strictly above the level's threshold."""
+    K, W = P.shape
+    out = []
+    for lev, thr in enumerate(thresholds):
+        H = (2, 4, 8)[lev]
+        for j in range(K):
+            for c in range(W):
+                tot, ok = 0.0, True
+                for h in range(1, H + 1):
+                    z = h * (zmin + j * zstep)
+                    if (z - zmin) % zstep:
+                        ok = False
+                        break
+                    row = (z - zmin) // zstep
+                    if not (0 <= row < K) or h * c >= W:
+                        ok = False
+                        break
+                    tot += P[row, h * c]
+                if ok and tot > thr:
+                    out.append((H, j, c, tot))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("zmin,zstep,K,W", [(-12, 3, 9, 41), (-20, 2, 21, 64), (0, 1, 6, 30)])
+def test_harmonic_candidates_match_brute_force(zmin, zstep, K, W):
+    rng = np.random.default_rng(K * W)
+    # integer-valued powers so that sums are exact and can equal a threshold
+    P = rng.integers(0, 6, (K, W)).astype(np.float64)
+    thresholds = (7.0, 13.0, 24.0)
+    rows, cols, sums, Hs = O.harmonic_candidates(P, zmin, zstep, thresholds)
+    got = sorted(zip(Hs.tolist(), rows.tolist(), cols.tolist(), sums.tolist()))
+    ref = _brute_harmonic_candidates(P, zmin, zstep, thresholds)
+    assert got == ref
+    # the strict comparison matters: some sums sit exactly on a threshold
+    ties = 0
+    for lev, thr in enumerate(thresholds):
+        S = O.harmonic_sum(P, zmin, zstep, 2 << lev)
+        ties += int(np.sum(S == thr))
+    assert ties > 0
+    # fundamentals whose harmonics leave the plane are never listed
+    for H, j, c, _ in got:
+        assert H * c < W and 0 <= (H - 1) * (zmin // zstep) + H * j < K
+
+
 # ---------------------------------------------------------------- significance
 def test_noise_means_closed_forms_at_z0():
     m1 = O.noise_means([0.0], 1)[0]
@@ -436,3 +483,51 @@ def test_noise_planes_are_exponential_with_the_predicted_means(interbin):
             assert abs(v.mean() / mu[k, e] - 1.0) < 0.03, (k, e, v.mean(), mu[k, e])
             tail = np.mean(v / mu[k, e] > 3.0)
             assert abs(tail - np.exp(-3.0)) < 0.006
+
+
+def _normal_log_tail_asymptotic(s):
+    """log P(N(0,1) > s) from the asymptotic series phi(s)/s (1 - 1/s^2 +
+    3/s^4 - 15/s^6 + 105/s^8), accurate to ~1e-18 relative at s = 100."""
+    u = 1.0 / (s * s)
+    series = 1.0 - u + 3 * u ** 2 - 15 * u ** 3 + 105 * u ** 4
+    return -0.5 * s * s - math.log(s * math.sqrt(2 * math.pi)) + math.log(series)
+
+
+def test_sigma_of_log_tail_matches_the_normal_table():
+    # upper-tail probabilities of the standard normal (tabulated values)
+    table = {1.0: 0.15865525393145705, 2.0: 0.022750131948179195,
+             3.0: 0.0013498980316300946, 5.0: 2.866515718791939e-07}
+    for s, q in table.items():
+        assert abs(O.sigma_of_log_tail(math.log(q)) - s) < 1e-12 * s
+    for s in (40.0, 100.0):
+        assert abs(O.sigma_of_log_tail(_normal_log_tail_asymptotic(s)) - s) < 1e-12 * s
+    assert O.sigma_of_log_tail(math.log(0.5)) == 0.0
+    assert O.sigma_of_log_tail(-0.1) == 0.0
+
+
+def test_exp_sum_tail_special_cases():
+    from scipy.special import gammaincc
+    # one exponential: exp(-x/m)
+    assert abs(O.exp_sum_log_tail(7.5, [1.5]) - (-5.0)) < 1e-14
+    # equal means: the Erlang (integer-shape gamma) tail
+    for H, x, m in ((2, 9.0, 1.0), (4, 30.0, 1.234), (8, 60.0, 1.0)):
+        assert abs(O.exp_sum_log_tail(x, [m] * H) / math.log(gammaincc(H, x / m)) - 1) < 1e-13
+    # two well-separated means: (m1 e^{-x/m1} - m2 e^{-x/m2}) / (m1 - m2) in FP64
+    m1, m2, x = 1.0, 3.0, 11.0
+    ref = math.log((m1 * math.exp(-x / m1) - m2 * math.exp(-x / m2)) / (m1 - m2))
+    assert abs(O.exp_sum_log_tail(x, [m1, m2]) / ref - 1) < 1e-14
+    # a tail is a probability, falls with x, and nearly equal means sit near the Erlang tail
+    a = [O.exp_sum_log_tail(x, [1.0, 1.001, 0.999, 1.002]) for x in (2.0, 8.0, 20.0)]
+    assert 0.0 > a[0] > a[1] > a[2]
+    e = math.log(gammaincc(4, 20.0))
+    assert abs(a[2] - e) < 0.01 * abs(e)
+
+
+def test_exp_sum_tail_monte_carlo():
+    rng = np.random.default_rng(91)
+    means = np.array([1.0, 1.05, 1.2337, 0.97])
+    s = (rng.exponential(1.0, (2_000_000, 4)) * means).sum(axis=1)
+    for x in (6.0, 10.0):
+        p = math.exp(O.exp_sum_log_tail(x, means))
+        n = int(np.sum(s > x))
+        assert abs(n - p * len(s)) < 5 * math.sqrt(p * len(s)), (x, n, p * len(s))
