@@ -142,7 +142,8 @@ int64_t series_items(const Grid& g, int L, int64_t npos) {
     int64_t items = 0;
     for (int k = 0; k < g.ng; ++k) {
         const int64_t B = L - g.gM[k];
-        items += ((npos + B - 1) / B) * g.gK[k];
+        const int64_t segs = (npos + B - 1) / B;
+        items += (L == 1024 ? (segs + 3) / 4 : segs) * g.gK[k];
     }
     return items;
 }
@@ -184,7 +185,7 @@ int32_t fdas_bank_rows(const fdas_params* p) {
 int64_t fdas_bank_floats(const fdas_params* p) {
     Grid g;
     int rc = make_grid(p, &g);
-    return rc == FDAS_OK ? (int64_t)g.Kb * (p->L + 16) * 2 : rc;
+    return rc == FDAS_OK ? (int64_t)g.Kb * bank_row_complex(p->L) * 2 : rc;
 }
 
 int64_t fdas_num_segments(const fdas_params* p, int64_t nb) {
@@ -272,7 +273,7 @@ int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, 
     Grid g;
     int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);
     if (rc != FDAS_OK) return rc;
-    if (prec != FDAS_PREC_FP32 && p->interbin == 2) return FDAS_E_UNSUPPORTED;
+    if (prec != FDAS_PREC_FP32 && (p->interbin == 2 || p->L == 1024)) return FDAS_E_UNSUPPORTED;
     if (prec == FDAS_PREC_FP32)
         return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
                                 reinterpret_cast<const float4*>(bank), plane, row_stride, fused,

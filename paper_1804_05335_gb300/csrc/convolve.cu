@@ -1,5 +1,5 @@
 // fdas_correlate and fdas_correlate_batched: launchers of the FP32 convolver
-// (kernel in conv_kernel.cuh).
+// (kernel in conv_kernel.cuh; L = 1024 goes to the warp convolver, wconv.cu).
 #include "conv_kernel.cuh"
 
 namespace fdas {
@@ -7,11 +7,9 @@ namespace fdas {
 template <bool BATCH>
 static int dispatch(const fdas_params* p, const ConvArgs& a, bool fused, int ctas_per_sm,
                     cudaStream_t st) {
+    if (p->L == 1024) return dispatch_wconv(p, a, fused, BATCH, 0, ctas_per_sm, st);
     if (p->interbin == 2) return dispatch_half_bins(p, a, fused, BATCH, ctas_per_sm, st);
     switch (p->L) {
-        case 1024:
-            return fused ? launch_one<1024, true, BATCH>(a, ctas_per_sm, st)
-                         : launch_one<1024, false, BATCH>(a, ctas_per_sm, st);
         case 2048:
             return fused ? launch_one<2048, true, BATCH>(a, ctas_per_sm, st)
                          : launch_one<2048, false, BATCH>(a, ctas_per_sm, st);

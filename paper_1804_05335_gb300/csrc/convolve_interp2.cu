@@ -8,9 +8,6 @@ template <bool BATCH>
 static int dispatch_sub2(const fdas_params* p, const ConvArgs& a, bool fused, int ctas_per_sm,
                          cudaStream_t st) {
     switch (p->L) {
-        case 1024:
-            return fused ? launch_one<1024, true, BATCH, 0, 0, 2>(a, ctas_per_sm, st)
-                         : launch_one<1024, false, BATCH, 0, 0, 2>(a, ctas_per_sm, st);
         case 2048:
             return fused ? launch_one<2048, true, BATCH, 0, 0, 2>(a, ctas_per_sm, st)
                          : launch_one<2048, false, BATCH, 0, 0, 2>(a, ctas_per_sm, st);

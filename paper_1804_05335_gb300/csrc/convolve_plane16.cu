@@ -9,8 +9,7 @@ template <int OUT>
 static int dispatch_plane16(const fdas_params* p, const ConvArgs& a, bool fused, cudaStream_t st) {
     switch (p->L) {
         case 1024:
-            return fused ? launch_one<1024, true, false, 0, OUT>(a, 0, st)
-                         : launch_one<1024, false, false, 0, OUT>(a, 0, st);
+            return dispatch_wconv(p, a, fused, false, OUT, 0, st);
         case 2048:
             return fused ? launch_one<2048, true, false, 0, OUT>(a, 0, st)
                          : launch_one<2048, false, false, 0, OUT>(a, 0, st);

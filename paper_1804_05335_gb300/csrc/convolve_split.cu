@@ -1,6 +1,6 @@
 // fdas_correlate_split: the convolver with its radix-16 DFT passes as
 // split-precision tensor-core products (kernel in conv_kernel.cuh, DFT in
-// split_mma.cuh).  Single-series launches only.
+// split_mma.cuh).  Single-series launches, L = 2048 and 4096.
 #include "conv_kernel.cuh"
 
 namespace fdas {
@@ -8,9 +8,6 @@ namespace fdas {
 template <int PREC>
 static int dispatch_split(const fdas_params* p, const ConvArgs& a, bool fused, cudaStream_t st) {
     switch (p->L) {
-        case 1024:
-            return fused ? launch_one<1024, true, false, PREC>(a, 0, st)
-                         : launch_one<1024, false, false, PREC>(a, 0, st);
         case 2048:
             return fused ? launch_one<2048, true, false, PREC>(a, 0, st)
                          : launch_one<2048, false, false, PREC>(a, 0, st);

@@ -1,4 +1,4 @@
-// Register-resident small DFTs (radix 2/4/8/16) used by the convolver and
+// Register-resident small DFTs (radix 2/4/8/16/32) used by the convolver and
 // the front end.  S = -1 is the forward transform  X_k = sum_n x_n e^{-i2pi nk/N},
 // S = +1 the inverse without 1/N  (DFT and IDFT of Section 4.2).  Inputs and
 // outputs are in natural order; all indices are compile-time constants so
@@ -165,6 +165,66 @@ __device__ __forceinline__ void dftq(float2* v) {
         static_assert(Q == 16, "radix");
         dft16<S>(v);
     }
+}
+
+
+// cos and sin of pi k / 16, k = 0..15 (for the 32-point DFT's twiddles)
+constexpr float kW32c[16] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                             0.83146961230254523708f, 0.70710678118654752440f,
+                             0.55557023301960222474f, 0.38268343236508977173f,
+                             0.19509032201612826785f, 0.0f, -0.19509032201612826785f,
+                             -0.38268343236508977173f, -0.55557023301960222474f,
+                             -0.70710678118654752440f, -0.83146961230254523708f,
+                             -0.92387953251128675613f, -0.98078528040323044913f};
+constexpr float kW32s[16] = {0.0f, 0.19509032201612826785f, 0.38268343236508977173f,
+                             0.55557023301960222474f, 0.70710678118654752440f,
+                             0.83146961230254523708f, 0.92387953251128675613f,
+                             0.98078528040323044913f, 1.0f, 0.98078528040323044913f,
+                             0.92387953251128675613f, 0.83146961230254523708f,
+                             0.70710678118654752440f, 0.55557023301960222474f,
+                             0.38268343236508977173f, 0.19509032201612826785f};
+
+// v * w32^K,  w32 = exp(S i 2 pi / 32),  0 <= K < 16 a compile-time constant
+template <int S, int K>
+__device__ __forceinline__ float2 w32(float2 v) {
+    if constexpr (K % 2 == 0) {
+        return w16<S, K / 2>(v);
+    } else {
+        constexpr float c = kW32c[K], s = (float)S * kW32s[K];
+        return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
+    }
+}
+
+// Last radix-2 layer of the 32-point DFT: X[K] = E[K] + w^K O[K],
+// X[K+16] = E[K] - w^K O[K] for K = KK..15 (w^8 = S i folded into the adds).
+template <int S, int KK>
+__device__ __forceinline__ void dft32_combine(float2* v, const float2* e, const float2* o) {
+    if constexpr (KK < 16) {
+        if constexpr (KK == 8) {
+            v[8] = add_si<S>(e[8], o[8]);
+            v[24] = sub_si<S>(e[8], o[8]);
+        } else {
+            const float2 t = w32<S, KK>(o[KK]);
+            v[KK] = e[KK] + t;
+            v[KK + 16] = e[KK] - t;
+        }
+        dft32_combine<S, KK + 1>(v, e, o);
+    }
+}
+
+// 32 points in natural order: 16-point DFTs of the even and the odd inputs,
+// then one radix-2 layer.
+template <int S>
+__device__ __forceinline__ void dft32(float2* v) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft16<S>(e);
+    dft16<S>(o);
+    dft32_combine<S, 0>(v, e, o);
 }
 
 }  // namespace fdas

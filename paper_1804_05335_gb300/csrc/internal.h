@@ -32,9 +32,16 @@ int make_grid(const fdas_params* p, Grid* g);
 // half-bin (2-bin Fourier interpolation) sampling.
 inline int64_t positions(const fdas_params* p, int64_t nb) { return p->interbin == 2 ? 2 * nb : nb; }
 
-// Work items (segment, template) of one series of npos positions: for each
-// group, ceil(npos / (L - gM)) segments times gK templates.
+// Work items of one series of npos positions.  L = 2048, 4096 (one CTA per
+// segment FFT): (segment, template) pairs, for each group ceil(npos / (L - gM))
+// segments times gK templates.  L = 1024 (one warp per segment FFT): units of
+// one template on four consecutive segments, ceil(segments / 4) times gK.
 int64_t series_items(const Grid& g, int L, int64_t npos);
+
+// Complex values per template-bank row: L = 1024 rows hold 16 register pairs
+// x 33 slots (32 lanes + a mirror column) of two values; longer segments hold
+// L digit-reversed values + 16 mirror slots.
+inline int bank_row_complex(int L) { return L == 1024 ? L + 32 : L + 16; }
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_E_CUDA; }
 
@@ -56,6 +63,11 @@ int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_tri
                              const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
                              cudaStream_t st);
 struct ConvArgs;
+// The L = 1024 (one warp per segment FFT) convolver, wconv.cu: element type
+// `out` (0 float, FDAS_PLANE_F16, FDAS_PLANE_BF16), half-bin sampling when
+// p->interbin == 2.
+int dispatch_wconv(const fdas_params* p, const ConvArgs& a, bool fused, bool batch, int out,
+                   int ctas_per_sm, cudaStream_t st);
 // The convolver with half-bin sampling (interbin 2), convolve_interp2.cu.
 int dispatch_half_bins(const fdas_params* p, const ConvArgs& a, bool fused, bool batch,
                        int ctas_per_sm, cudaStream_t st);

@@ -1,0 +1,493 @@
+// The L = 1024 overlap-save convolver: one warp per segment FFT (Sections 3,
+// 4.1, 4.2).
+//
+// A CTA of NW = 4 warps takes a contiguous, statically balanced range of work
+// units in the order (series, template group, quad, template): a unit is one
+// template applied to the quad's four consecutive segments, one per warp.
+// When the quad changes, each warp loads its segment -- L bins starting at
+// s*B - M/2, zero outside the spectrum -- and runs the forward FFT once
+// (wfft.cuh), keeping the spectrum Y in registers.  Per unit, each warp
+// multiplies Y by the template spectrum, runs the inverse FFT, forms full-
+// and half-bin powers of its B useful positions and writes them to the plane.
+// The whole transform stays inside the warp: one exchange through the warp's
+// shared memory, no CTA barrier.
+//
+// Template rows are staged by bulk copies (cp.async.bulk) into NBUF shared
+// buffers, each read by all four warps: one thread issues the copies in the
+// order the units need them, a `full` mbarrier per buffer completes on the
+// copy's bytes, and an `empty` mbarrier per buffer collects one arrival per
+// warp when the warp is done with the row.  A symmetric grid pairs +z and -z
+// in consecutive units on one row (H_{-z}[k] = conj(H_z[-k]), Section 4.2):
+// -k of lane l, register i is lane 32 - l, register 31 - i (l >= 1); lane 0's
+// values at -k sit in the row's mirror column, so every lane reads the
+// conjugate row at 527 - 33 j - l.
+//
+// Epilogue: position p = l + 32 i of register i; the half bin needs x[p + 1],
+// which lane l + 1 holds in the same register, passed by one shuffle per
+// component.  Lane 31's neighbour is lane 0's next register, so lane 0
+// supplies that one instead (32 lanes in a cycle cannot all find p + 1 in
+// the same register of the next lane).  Each warp store covers 32
+// consecutive bins (256 contiguous bytes with interbinning).
+//
+// Every wait is bounded.  A wait that runs out (or `A.probe` set, which arms
+// the first row's barrier without issuing its copy -- a diagnostic that makes
+// the wait run out with nothing in flight) sets FDAS_STATUS_TIMEOUT, stops
+// every warp of the CTA through a shared flag, and the copy-issuing thread
+// waits, again bounded, for its copies still in flight before the CTA exits.
+#pragma once
+#include "conv_common.cuh"
+#include "tma.cuh"
+#include "wfft.cuh"
+
+namespace fdas {
+
+struct WSmem {
+    static constexpr size_t bytes =
+        (size_t)WShape::NBUF * WShape::ROW4 * sizeof(float4) +     // staged bank rows
+        (size_t)WShape::TW4 * sizeof(float4) +                       // twiddle table
+        (size_t)WShape::NW * WShape::XBUF * sizeof(float2);          // per-warp exchange
+};
+
+template <int I>
+struct Ic {
+    static constexpr int value = I;
+};
+// f(Ic<I>{}) for I = I0 .. I1 - 1, unrolled at compile time
+template <int I0, int I1, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I0 < I1) {
+        f(Ic<I0>{});
+        static_for<I0 + 1, I1>(f);
+    }
+}
+
+// The series of the unit being processed: a single-series launch reads it
+// from the launch arguments (no registers held), a batched launch from the
+// trial table.
+template <bool BATCH>
+struct WSeries {
+    __device__ __forceinline__ void set(const ConvArgs&, int) {}
+    __device__ __forceinline__ const float2* spec(const ConvArgs& A) const { return A.spec; }
+    __device__ __forceinline__ int64_t nb(const ConvArgs& A) const { return A.nb; }
+    __device__ __forceinline__ float* plane(const ConvArgs& A) const { return A.plane; }
+    __device__ __forceinline__ int64_t row_stride(const ConvArgs& A) const { return A.row_stride; }
+    __device__ __forceinline__ int64_t end(const ConvArgs& A) const { return A.items; }
+    __device__ __forceinline__ int flags() const { return 0; }
+    __device__ __forceinline__ int trial() const { return 0; }
+};
+template <>
+struct WSeries<true> {
+    SeriesState st;
+    int tr;
+    __device__ __forceinline__ void set(const ConvArgs& A, int t) {
+        tr = t;
+        st = series_of<true>(A, t);
+    }
+    __device__ __forceinline__ const float2* spec(const ConvArgs&) const { return st.spec; }
+    __device__ __forceinline__ int64_t nb(const ConvArgs&) const { return st.nb; }
+    __device__ __forceinline__ float* plane(const ConvArgs&) const { return st.plane; }
+    __device__ __forceinline__ int64_t row_stride(const ConvArgs&) const { return st.row_stride; }
+    __device__ __forceinline__ int64_t end(const ConvArgs&) const { return st.end; }
+    __device__ __forceinline__ int flags() const { return st.flags; }
+    __device__ __forceinline__ int trial() const { return tr; }
+};
+
+// Walk over the work units of a series (or of a batch of series).
+template <bool BATCH, int SUB>
+struct WWalk {
+    int64_t u;        // unit index
+    WSeries<BATCH> ser;
+    int nq;           // quads of group grp in the current series
+    int quad;         // segments 4 quad .. 4 quad + 3 of group grp
+    int grp;
+    int q;            // template of group grp
+
+    __device__ __forceinline__ int64_t npos(const ConvArgs& A) const { return SUB * ser.nb(A); }
+    __device__ __forceinline__ int quads(const ConvArgs& A, int g) const {
+        const int64_t B = WShape::L - A.gM[g];
+        return (int)(((npos(A) + B - 1) / B + WShape::NW - 1) / WShape::NW);
+    }
+    __device__ __forceinline__ void init(const ConvArgs& A, int64_t u0) {
+        u = u0;
+        int trial = 0;
+        if constexpr (BATCH) {   // last trial whose first unit is <= u0
+            int a0 = 0, a1 = A.ntrials - 1;
+            while (a0 < a1) {
+                const int mid = (a0 + a1 + 1) >> 1;
+                if (A.trials[mid].item_begin <= u0) a0 = mid; else a1 = mid - 1;
+            }
+            trial = a0;
+        }
+        ser.set(A, trial);
+        int64_t rel = u0 - (BATCH ? A.trials[trial].item_begin : 0);
+        grp = 0;
+        nq = quads(A, 0);
+        while (rel >= (int64_t)nq * A.gK[grp] && grp + 1 < A.ng) {
+            rel -= (int64_t)nq * A.gK[grp];
+            ++grp;
+            nq = quads(A, grp);
+        }
+        quad = (int)(rel / A.gK[grp]);
+        q = (int)(rel - (int64_t)quad * A.gK[grp]);
+    }
+    // next unit; returns true if it starts a new quad (new segments)
+    __device__ __forceinline__ bool advance(const ConvArgs& A) {
+        ++u;
+        bool fresh = false;
+        if (++q == A.gK[grp]) {
+            q = 0;
+            fresh = true;
+            if (++quad == nq) {
+                quad = 0;
+                if (++grp == A.ng) grp = 0;
+                nq = quads(A, grp);
+            }
+        }
+        if constexpr (BATCH) {
+            if (u == ser.end(A) && u < A.items) {
+                ser.set(A, ser.trial() + 1);
+                grp = 0;
+                quad = 0;
+                q = 0;
+                nq = quads(A, 0);
+                fresh = true;
+            }
+        }
+        return fresh;
+    }
+};
+
+template <bool BATCH, int SUB>
+struct WProducer {            // state of the copy-issuing thread, in shared memory
+    WWalk<BATCH, SUB> walk;   // first unit whose row is not yet issued
+    uint32_t issued;          // rows issued so far
+};
+
+// Bounded wait on phase `parity` of `bar`; gives up early when `abort` is set.
+__device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, const volatile int* abort,
+                                      uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16-bit or float plane stores of one or two consecutive elements (elements
+// of type OUT; the two-element store needs 2-element alignment).
+template <int OUT>
+__device__ __forceinline__ void wstore2(void* row, int64_t i, float a, float b) {
+    if constexpr (OUT == 0) {
+        __stcs(reinterpret_cast<float2*>(static_cast<float*>(row) + i), make_float2(a, b));
+    } else {
+        uint32_t u;
+        if constexpr (OUT == 1) {
+            __half2 h = __floats2half2_rn(a, b);
+            u = *reinterpret_cast<uint32_t*>(&h);
+        } else {
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            u = *reinterpret_cast<uint32_t*>(&h);
+        }
+        __stcs(reinterpret_cast<unsigned int*>(static_cast<uint16_t*>(row) + i), u);
+    }
+}
+template <int OUT>
+__device__ __forceinline__ void wstore1(void* row, int64_t i, float a) {
+    if constexpr (OUT == 0) {
+        __stcs(static_cast<float*>(row) + i, a);
+    } else if constexpr (OUT == 1) {
+        reinterpret_cast<__half*>(row)[i] = __float2half_rn(a);
+    } else {
+        reinterpret_cast<__nv_bfloat16*>(row)[i] = __float2bfloat16_rn(a);
+    }
+}
+
+constexpr float kHalfBinScale = 0.61685027506808491f;   // (pi/4)^2 of Eq. f-interp
+
+// Powers of the 32 registers of one lane after wfft_inverse, for a segment
+// that lies inside the series with M/2 <= 160: registers 5..26 always hold
+// useful positions; the lane's useful registers are ilo .. ihi - 1 (ilo <= 5,
+// ihi >= 27).  IB: full bin and interbinned half bin per position (x[p + 1]
+// from lane l + 1, same register), else the full bin.  rb: the bin of
+// register 0.  Returns the lane's largest power.
+template <int OUT, bool IB>
+__device__ __forceinline__ float wepi_fast(const float2* v, int l, int ilo, int ihi, void* prow,
+                                           int64_t rb) {
+    float mx = 0.f;
+    static_for<0, 32>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        bool ok;
+        if constexpr (i >= 5 && i <= 26) ok = true;
+        else if constexpr (i < 5) ok = i >= ilo;
+        else ok = i < ihi;
+        const float2 x = v[i];
+        const float pf = fmaf(x.x, x.x, x.y * x.y);
+        if constexpr (IB) {
+            const float2 pv = (l == 0) ? v[(i + 1) & 31] : x;   // lane 31's neighbour
+            float2 xn;
+            xn.x = __shfl_sync(0xffffffffu, pv.x, (l + 1) & 31);
+            xn.y = __shfl_sync(0xffffffffu, pv.y, (l + 1) & 31);
+            const float2 d = x - xn;
+            const float ph = kHalfBinScale * fmaf(d.x, d.x, d.y * d.y);
+            if (ok) {
+                wstore2<OUT>(prow, 2 * (rb + 32 * i), pf, ph);
+                mx = fmaxf(mx, fmaxf(pf, ph));
+            }
+        } else {
+            if (ok) {
+                wstore1<OUT>(prow, rb + 32 * i, pf);
+                mx = fmaxf(mx, pf);
+            }
+        }
+    });
+    return mx;
+}
+
+// The general epilogue (a segment reaching the end of the series, overlaps
+// above 320) and the listing pass of the fused threshold: the lane's
+// registers are staged in position order in the warp's exchange buffer, then
+// positions M2 + l, M2 + l + 32, ... below pend are walked by a rolled loop,
+// each checked against the series end.  SCAN: list the values above A.thr
+// instead of storing.  Returns the lane's largest stored power.
+template <int OUT, bool IB, bool SCAN>
+__device__ __forceinline__ float wepi_staged(const float2* v, float2* xb, int l, int M2, int pend,
+                                             int64_t r0, int64_t npos, void* prow,
+                                             const ConvArgs& A, int row, int flags) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) xb[l + 32 * i] = v[i];
+    __syncwarp();
+    float mx = 0.f;
+#pragma unroll 1
+    for (int p = M2 + l; p < pend; p += 32) {
+        const int64_t r = r0 + (p - M2);
+        if (r >= npos) break;
+        const float2 x = xb[p];
+        const float pf = fmaf(x.x, x.x, x.y * x.y);
+        if constexpr (IB) {
+            const float2 d = x - xb[p + 1];
+            // the last bin of the series has no r + 1: its half bin is 0
+            const float ph = r + 1 < npos ? kHalfBinScale * fmaf(d.x, d.x, d.y * d.y) : 0.f;
+            if constexpr (SCAN) {
+                if (pf > A.thr) emit(A, row, 2 * r, pf, flags);
+                if (ph > A.thr) emit(A, row, 2 * r + 1, ph, flags);
+            } else {
+                wstore2<OUT>(prow, 2 * r, pf, ph);
+                mx = fmaxf(mx, fmaxf(pf, ph));
+            }
+        } else {
+            if constexpr (SCAN) {
+                if (pf > A.thr) emit(A, row, r, pf, flags);
+            } else {
+                wstore1<OUT>(prow, r, pf);
+                mx = fmaxf(mx, pf);
+            }
+        }
+    }
+    __syncwarp();
+    return mx;
+}
+
+// Forward FFT of one segment (a warp's, once per quad): positions base + l +
+// 32 i of the series (zero outside it; SUB = 2: the spectrum with zeros
+// interleaved, npos = 2 nb), transformed by wfft_forward and left in the
+// warp's buffer as xb[i*32 + l] = X[l + 32 i].  Not inlined: it runs once
+// per quad, and keeping its code out of the per-template loop keeps that
+// loop small in the instruction cache.
+template <int SUB>
+__device__ __noinline__ void wseg_forward(const float2* __restrict__ spec, int64_t nb, int64_t base,
+                                          float2* xb, const float4* tw4, int l) {
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int64_t pos = base + l + 32 * i;
+        if constexpr (SUB == 1) {
+            v[i] = (pos >= 0 && pos < nb) ? __ldg(&spec[pos]) : make_float2(0.f, 0.f);
+        } else {
+            v[i] = (pos >= 0 && pos < 2 * nb && !(pos & 1)) ? __ldg(&spec[pos >> 1])
+                                                             : make_float2(0.f, 0.f);
+        }
+    }
+    wfft_forward(v, xb, tw4, l);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) xb[i * 32 + l] = v[i];
+    __syncwarp();
+}
+
+template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB>
+__global__ void __launch_bounds__(WShape::NW * 32, 3) wconv_kernel(const ConvArgs A) {
+    constexpr int NW = WShape::NW, NBUF = WShape::NBUF, ROW4 = WShape::ROW4, L = WShape::L;
+    extern __shared__ float4 wsm4[];
+    float4* hbuf = wsm4;                                   // NBUF rows of ROW4
+    float4* tw4 = hbuf + NBUF * ROW4;
+    float2* xall = reinterpret_cast<float2*>(tw4 + WShape::TW4);
+    __shared__ uint64_t full[NBUF], empty[NBUF];
+    __shared__ volatile int abort_flag;
+    __shared__ WProducer<BATCH, SUB> prod;
+
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    float2* xb = xall + w * WShape::XBUF;
+    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
+    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
+    if (lo >= hi) return;
+    const uint32_t limit = A.wait_limit ? A.wait_limit : kWaitLimit;   // copy-issuing thread
+
+    WWalk<BATCH, SUB> cw;
+    cw.init(A, lo);
+
+    // issue the copies of rows up to `target` (thread 0 only)
+    auto produce = [&](uint32_t target) {
+        while (prod.issued <= target && prod.walk.u < hi) {
+            const uint32_t k = prod.issued, b = k % NBUF;
+            if (k >= NBUF && !wwait(&empty[b], ((k / NBUF) - 1) & 1, &abort_flag, limit)) {
+                if (!abort_flag && A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
+                abort_flag = 1;
+                return;
+            }
+            int row, brow, cj;
+            item_row(A, prod.walk.grp, prod.walk.q, row, brow, cj);
+            fence_proxy_async();
+            if (A.probe && k == 0) {   // diagnostic: armed, never filled
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             ::"r"(smem_u32(&full[b])), "r"((uint32_t)(ROW4 * sizeof(float4)))
+                             : "memory");
+            } else {
+                tma_load_1d(hbuf + b * ROW4, A.bank + (size_t)brow * ROW4,
+                            ROW4 * sizeof(float4), &full[b]);
+            }
+            prod.issued = k + 1;
+            // skip the units that use the same row (a +-z pair, a one-row group)
+            int r2, b2 = brow, c2;
+            do {
+                prod.walk.advance(A);
+                if (prod.walk.u >= hi) break;
+                item_row(A, prod.walk.grp, prod.walk.q, r2, b2, c2);
+            } while (b2 == brow);
+        }
+    };
+
+    wfft_twiddles(tw4, tid, NW * 32);
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], NW);
+        }
+        abort_flag = 0;
+        prod.walk = cw;
+        prod.issued = 0;
+        produce(NBUF - 1);
+    }
+    __syncthreads();
+
+    float2 Y[32], v[32];
+    bool fresh = true, live = false, fast = false;
+    int cur_brow = -1, M2 = 0, B = 0, ilo = 0, ihi = 32;
+    int64_t r0 = 0, npos = 0;
+    uint32_t ri = 0xffffffffu;   // index of the row in use
+    while (cw.u < hi) {
+        int row, brow, cj;
+        item_row(A, cw.grp, cw.q, row, brow, cj);
+        if (fresh) {
+            // ---- a new quad: this warp's segment, its geometry and forward FFT ----
+            M2 = A.gM[cw.grp] / 2;
+            B = L - 2 * M2;
+            npos = cw.npos(A);
+            r0 = ((int64_t)cw.quad * NW + w) * B;   // bin of position M/2
+            live = r0 < npos;
+            fast = M2 <= 160 && r0 + B <= npos;
+            ilo = (M2 - l + 31) >> 5;               // first register at position >= M/2
+            ihi = (L - M2 - l + 31) >> 5;           // first register at position >= M/2 + B
+            if (live) {
+                wseg_forward<SUB>(cw.ser.spec(A), cw.ser.nb(A), r0 - M2, xb, tw4, l);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) Y[i] = xb[i * 32 + l];
+                __syncwarp();
+            }
+        }
+        if (brow != cur_brow) {
+            // ---- release the previous row, wait for this one ----
+            if (cur_brow >= 0) {
+                __syncwarp();
+                if (l == 0) mbar_arrive(&empty[ri % NBUF]);
+            }
+            ++ri;
+            cur_brow = brow;
+            if (tid == 0) produce(ri + NBUF - 1);
+            const bool got = wwait(&full[ri % NBUF], (ri / NBUF) & 1, &abort_flag,
+                                   A.wait_limit ? A.wait_limit : kWaitLimit);
+            if (!__all_sync(0xffffffffu, got)) {   // the warp leaves together
+                if (l == 0) {
+                    if (!abort_flag && A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
+                    abort_flag = 1;
+                }
+                break;
+            }
+        }
+        if (live) {
+            // ---- multiply by the template spectrum ----
+            const float4* hr = hbuf + (ri % NBUF) * ROW4;
+            if (!cj) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float4 h = hr[j * 33 + l];
+                    v[2 * j] = cmul(Y[2 * j], make_float2(h.x, h.y));
+                    v[2 * j + 1] = cmul(Y[2 * j + 1], make_float2(h.z, h.w));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float4 h = hr[527 - 33 * j - l];
+                    v[2 * j] = cmulc(Y[2 * j], make_float2(h.z, h.w));
+                    v[2 * j + 1] = cmulc(Y[2 * j + 1], make_float2(h.x, h.y));
+                }
+            }
+            // ---- inverse FFT ----
+            wfft_inverse(v, xb, tw4, l);
+            // ---- powers of positions M/2 .. M/2 + B - 1 ----
+            void* prow = OUT == 0 ? static_cast<void*>(cw.ser.plane(A) + (int64_t)row * cw.ser.row_stride(A))
+                                  : static_cast<void*>(reinterpret_cast<uint16_t*>(cw.ser.plane(A)) +
+                                                       (int64_t)row * cw.ser.row_stride(A));
+            float mx;
+            if (fast) {
+                mx = wepi_fast<OUT, IB>(v, l, ilo, ihi, prow, r0 - M2 + l);
+            } else {
+                mx = wepi_staged<OUT, IB, false>(v, xb, l, M2, L - M2, r0, npos, prow, A, row, 0);
+            }
+            if constexpr (FUSE) {
+                if (__any_sync(0xffffffffu, mx > A.thr))   // rare: list the crossings
+                    wepi_staged<OUT, IB, true>(v, xb, l, M2, L - M2, r0, npos, prow, A, row,
+                                               cw.ser.flags());
+            }
+        }
+        fresh = cw.advance(A);
+    }
+
+    if (tid == 0 && abort_flag) {
+        // no copy may still be writing this CTA's shared memory when it exits
+        const uint32_t n = prod.issued;
+        for (uint32_t k = (n > NBUF ? n - NBUF : 0); k < n; ++k) {
+            if (A.probe && k == 0) continue;   // armed without a copy: nothing in flight
+            const int never = 0;
+            wwait(&full[k % NBUF], (k / NBUF) & 1, &never, limit);
+        }
+    }
+}
+
+template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB>
+static int launch_w(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
+    constexpr size_t smem = WSmem::bytes;
+    int sms = 0, max_per_sm = 0;
+    const int rc = kernel_setup(
+        reinterpret_cast<const void*>(&wconv_kernel<FUSE, BATCH, OUT, SUB, IB>), smem,
+        WShape::NW * 32, &sms, &max_per_sm);
+    if (rc != FDAS_OK) return rc;
+    const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
+    const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
+    wconv_kernel<FUSE, BATCH, OUT, SUB, IB><<<(unsigned)g, WShape::NW * 32, smem, st>>>(args);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace fdas

@@ -14,7 +14,17 @@ def bank_slot(k, L):
 
 def bank_natural(bank_f32, Kb, L):
     """(Kb, L) complex128 template spectra in natural frequency order, and the
-    (Kb, 16) mirror slots, both restated from the layout in fdas.h."""
+    mirror slots ((Kb, 16), or (Kb, 32) for L = 1024), both restated from the
+    layouts in fdas.h."""
+    if L == 1024:
+        # float4 slot j*33 + l = (H[l + 64 j], H[l + 64 j + 32]); slot j*33 + 32 is
+        # the mirror column
+        b = np.asarray(bank_f32, np.float32).reshape(Kb, 16, 33, 2, 2)
+        c = b[..., 0].astype(np.float64) + 1j * b[..., 1].astype(np.float64)
+        j, l, e = np.meshgrid(np.arange(16), np.arange(32), np.arange(2), indexing="ij")
+        H = np.empty((Kb, L), np.complex128)
+        H[:, (l + 64 * j + 32 * e).ravel()] = c[:, :, :32, :].reshape(Kb, -1)
+        return H, c[:, :, 32, :].reshape(Kb, 32)
     b = np.asarray(bank_f32, np.float32).reshape(Kb, L + 16, 2)
     c = b[..., 0].astype(np.float64) + 1j * b[..., 1].astype(np.float64)
     return c[:, bank_slot(np.arange(L), L)], c[:, L:]
@@ -23,7 +33,14 @@ def bank_natural(bank_f32, Kb, L):
 def mirror_expected(H, L):
     """Expected mirror slots from natural-order spectra H (Kb, L): complex
     L + 2j + 1 - e holds H[-k(s)] for slot s = 2(7 - j)T + e (T = L/16), the
-    slot of register 2(7 - j) + e of thread 0."""
+    slot of register 2(7 - j) + e of thread 0.  L = 1024: the mirror column's
+    float4 j holds (H[64 j + 32], H[(64 j + 64) mod 1024])."""
+    if L == 1024:
+        out = np.empty((H.shape[0], 32), H.dtype)
+        for j in range(16):
+            out[:, 2 * j] = H[:, 64 * j + 32]
+            out[:, 2 * j + 1] = H[:, (64 * j + 64) % L]
+        return out
     T = L // 16
     slot_k = np.empty(L, np.int64)
     slot_k[bank_slot(np.arange(L), L)] = np.arange(L)

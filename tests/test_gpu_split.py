@@ -47,12 +47,11 @@ def _within(got, ref, prec):
 
 CASES = [
     # n, L, M, zmin, zmax, zstep, interbin
-    (1 << 14, 1024, 64, -20, 20, 2, 1),      # ragged tail
-    (1 << 14, 2048, 64, -20, 20, 2, 1),
+    (1 << 14, 2048, 64, -20, 20, 2, 1),      # ragged tail
     (1 << 14, 4096, 128, -20, 20, 2, 1),
     (1 << 14, 2048, 64, -21, 21, 2, 1),      # symmetric grid without z = 0
     (1 << 14, 2048, 128, -10, 30, 5, 1),     # asymmetric grid: no conjugation
-    (1 << 14, 1024, 64, -20, 20, 2, 0),      # no interbinning
+    (1 << 14, 2048, 64, -20, 20, 2, 0),      # no interbinning
     (1 << 13, 4096, 256, -6, 6, 2, 1),       # one segment longer than the spectrum
 ]
 
@@ -71,6 +70,16 @@ def test_split_plane_matches_oracle(F, prec, n, L, M, zmin, zmax, zstep, ib):
     ref = O.plane(A.astype(np.complex128), O.z_grid(zmin, zmax, zstep), bool(ib))
     ok, emax = _within(got, ref, prec)
     assert ok, (NAMES[prec], emax)
+
+
+def test_split_rejects_warp_segment_length(F):
+    """L = 1024 runs the one-warp-per-segment convolver, which has no split form."""
+    S = _search(n=1 << 14, L=1024, M=64, zmin=-20, zmax=20, zstep=2)
+    S.make_templates()
+    for prec in (1, 2):
+        with pytest.raises(F.FdasError) as e:
+            S.correlate(fused=False, prec=prec)
+        assert e.value.code == F.FDAS_E_UNSUPPORTED
 
 
 def test_split_fp32_entry_is_fdas_correlate(F):
@@ -112,7 +121,7 @@ def test_fp16_split_keeps_range_on_strong_lines(F):
     A[1500] += 1.0e5
     A[4200] -= 7.0e4j
     A = A.astype(np.complex64)
-    S = _search(n=2 * nb, L=1024, M=64, zmin=-20, zmax=20, zstep=2)
+    S = _search(n=2 * nb, L=2048, M=64, zmin=-20, zmax=20, zstep=2)
     S.spec[:nb].copy_(torch.from_numpy(A))
     S.make_templates()
     S.correlate(fused=False, nb=nb, prec=1)
