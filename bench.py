@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--batch-trials", type=int, default=256)
     ap.add_argument("--rows", default="a8,a9,f1,f2,f3,f4,a11,a10",
                     help="scope rows measured after the timed steps (comma list)")
-    ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2],
-                    help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo")
+    ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo, "
+                         "3 BF16 hi+mid+lo (split forms need --L 2048 or 4096)")
     return ap.parse_args()
 
 
@@ -138,21 +139,26 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def conv_source_sha():
+def conv_source_sha(L=2048):
+    """Hash of the source files of the convolver that runs segments of L."""
+    files = (("wconv_kernel.cuh", "wfft.cuh", "conv_common.cuh", "dft.cuh", "tma.cuh", "wconv.cu")
+             if L == 1024 else
+             ("conv_kernel.cuh", "conv_common.cuh", "conv_fft.cuh", "dft.cuh", "tma.cuh",
+              "convolve.cu"))
     h = hashlib.sha256()
-    for f in ("conv_kernel.cuh", "conv_fft.cuh", "dft.cuh", "tma.cuh", "convolve.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1804_05335_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key):
+def recorded_traffic(kernel_key, L):
     """DRAM bytes per launch from a committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh).get(kernel_key)
-        if rec and rec.get("source_sha") == conv_source_sha():
+        if rec and rec.get("source_sha") == conv_source_sha(L):
             return float(rec["dram_bytes_per_launch"])
     except Exception:  # noqa: BLE001
         pass
@@ -578,17 +584,26 @@ def significance_row(args, torch, dev, S, wl):
 
 def split_row(args, torch, dev, S, wl):
     """The production plane with the four radix-16 DFT passes of every segment
-    FFT on tensor cores (FP16 and BF16 hi+lo operands, FP32 accumulation):
-    convolver time, and plane and candidate-list differences against the FP32
-    form on the same spectrum (errors against the FP64 oracle come from
-    tests/report_split_error.py)."""
+    FFT on tensor cores (FP16 hi+lo, BF16 hi+lo and BF16 hi+mid+lo operands,
+    FP32 accumulation): convolver time, and plane and candidate-list
+    differences against the FP32 form on the same spectrum (errors against the
+    FP64 oracle come from tests/test_gpu_split.py::test_split_production_error_table).
+    The split forms exist for L = 2048 and 4096; a step at L = 1024 is
+    measured here on its spectrum at L = 2048."""
+    if S.L == 1024:
+        from paper_1804_05335_gb300.search import Search
+        S2 = Search(wl.n, 2048, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
+                    median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
+        S2.spec.copy_(S.spec)
+        S2.make_templates()
+        S = S2
     S.correlate(fused=True)
     rf, cf, pf, _, _ = S.candidates()
     fp32 = {(int(r), int(c)) for r, c in zip(rf, cf)}
     ref = S.plane.clone()
     out = {}
     reps = 10
-    for name, prec in (("fp32", 0), ("fp16_split", 1), ("bf16_split", 2)):
+    for name, prec in (("fp32", 0), ("fp16_split", 1), ("bf16_split", 2), ("bf16x3_split", 3)):
         for _ in range(3):
             S.correlate(fused=True, prec=prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -614,7 +629,8 @@ def split_row(args, torch, dev, S, wl):
     del ref
     return {"workload": "production plane, L=%d" % S.L, "reps": reps, "forms": out,
             "dft_passes_on_tensor_cores": "radix-16 passes of forward and inverse FFTs "
-                                          "(mma.sync m16n8k16, 3 products per pass)"}
+                                          "(mma.sync m16n8k16; 3 products per pass, 6 for "
+                                          "bf16x3)"}
 
 
 def refine_row(args, torch, dev, S, wl):
@@ -752,12 +768,14 @@ def run_native(args):
         conv_mean = statistics.mean(conv_ms)
         alg_bytes = S.K * S.width * 4 + S.nb * 8 + S.Kb * S.L * 8
         achieved = alg_bytes / (conv_mean / 1e3) / 1e9
-        key = "conv_kernel<%d,true>" % wl.L + ("" if args.prec == 0 else "/prec%d" % args.prec)
+        key = ("wconv_kernel<fused,fp32,interbin>" if wl.L == 1024 else
+               "conv_kernel<%d,true>" % wl.L) + ("" if args.prec == 0 else "/prec%d" % args.prec)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {0: "f32", 1: "f16x2-split+f32", 2: "bf16x2-split+f32"}[args.prec],
+            "dtype": {0: "f32", 1: "f16x2-split+f32", 2: "bf16x2-split+f32",
+                      3: "bf16x3-split+f32"}[args.prec],
             "data": "synthetic",
             "config": {"workload": describe(wl), "n": wl.n, "nb": wl.nb, "K": S.K, "L": wl.L,
                        "M": wl.M, "segments": S.nseg, "plane_points": points,
@@ -765,7 +783,7 @@ def run_native(args):
                        "l2": "flushed between timed steps (256 MiB write); plane 6.7 GB > L2"},
             "roofline": {"bound": "hbm", "kernel": key, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": recorded_traffic(key),
+                         "traffic": recorded_traffic(key, wl.L),
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                          if peak_kind == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": alg_bytes,

@@ -124,7 +124,8 @@ int32_t fdas_num_templates(const fdas_params *p);
  * the number of negative z in a symmetric grid and 0 otherwise. */
 int32_t fdas_bank_rows(const fdas_params *p);
 
-/* Size of the template bank in floats: fdas_bank_rows(p) * (L + 16) * 2. */
+/* Size of the template bank in floats: fdas_bank_rows(p) * R * 2, with R =
+ * L + 32 complex values per row for L = 1024 and L + 16 otherwise. */
 int64_t fdas_bank_floats(const fdas_params *p);
 
 /* Number of overlap-save segments for nb bins at overlap M: ceil(nb / (L - M)). */
@@ -158,8 +159,9 @@ int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
  * for d = -h..h, the FIR kernel g[j] = conj(R_z(-j)) is placed circularly
  * (j >= 0 at the start, j < 0 at the end, zeros between) and
  *   H_z[k] = (1/L) sum_j g[j] exp(-i 2 pi j k / L),  k = 0..L-1
- * is stored in FP32 in the convolver's digit-reversed order.  A bank row is
- * L + 16 complex values (fdas_bank_floats gives the total size):
+ * is stored in FP32 in the order the convolver for L reads it.
+ * L = 2048, 4096 (one CTA per segment FFT): digit-reversed; a row is
+ * L + 16 complex values:
  *   bank[(b*(L+16) + s)*2 + {0,1}] = H_z[k(s)] (re, im), slot s = 0..L-1,
  *   with Q = L/256, T = L/16, s = 2*(ip*T + t) + e, i = 2*ip + e,
  *   t = a*Q + c1, i = s2*Q + c2  ->  k(s) = a + 16*(c1 + Q*s2) + 256*c2;
@@ -167,6 +169,12 @@ int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
  *   -k mod L: complex L + 2*j + 1 - e holds H_z[-k(s)] of slot
  *   s = 2*(7-j)*T + e (j = 0..7, e = 0..1), which lets conjugated templates
  *   be read with one access pattern for every thread.
+ * L = 1024 (one warp per segment FFT, lane l holding k = l + 32 i in
+ * register i): a row is 16 x 33 complex pairs (L + 32 complex values); pair
+ * j*33 + l (l < 32) holds (H_z[l + 64 j], H_z[l + 64 j + 32]) and pair
+ * j*33 + 32 holds (H_z[64 j + 32], H_z[(64 j + 64) mod 1024]), the values
+ * lane 0 needs for a conjugated template, so that every lane reads a
+ * conjugated row at pair 527 - 33 j - l.
  * bank: (device) fdas_bank_floats(p) floats, 16-byte aligned; written.
  * Errors: FDAS_E_INVAL for bad params or NULL bank.
  */
@@ -244,6 +252,24 @@ int fdas_normalise_noalloc(const float *series, int64_t n, int32_t median_block,
 int fdas_correlate(const fdas_params *p, const float *spec, int64_t nb, const float *bank,
                    float *plane, int64_t row_stride, const fdas_fused_threshold *fused,
                    int32_t *status, void *stream);
+
+/*
+ * fdas_debug_wait_timeout -- a diagnostic of the convolver's failure path,
+ * not a search.  Every wait of the convolver is bounded; this call runs the
+ * L = 1024 convolver (interbin 0 or 1) on the same arguments as
+ * fdas_correlate but arms the first template row's barrier in every CTA
+ * without issuing the row's copy, and lets each wait poll `polls` times
+ * (1 .. 2^24).  The first wait of every CTA therefore runs out with nothing
+ * in flight: the kernel ORs FDAS_STATUS_TIMEOUT into *status, stops all of
+ * its warps, waits (bounded) for the copies it did issue, and returns.  The
+ * plane is left with unspecified contents; the device stays usable.
+ * status: (device) int32, required.  Errors: FDAS_E_INVAL (as fdas_correlate,
+ * NULL status, polls out of range), FDAS_E_UNSUPPORTED (L != 1024 or
+ * interbin 2).
+ */
+int fdas_debug_wait_timeout(const fdas_params *p, const float *spec, int64_t nb, const float *bank,
+                            float *plane, int64_t row_stride, uint32_t polls, int32_t *status,
+                            void *stream);
 
 /* 16-bit plane element types (fdas_correlate_plane16). */
 #define FDAS_PLANE_F16 1        /* IEEE binary16: 11 significant bits, largest finite 65504 */
@@ -335,11 +361,12 @@ int fdas_noise_means(const fdas_params *p, float *means, void *stream);
 #define FDAS_PREC_FP32 0        /* FP32 on the CUDA cores, as fdas_correlate */
 #define FDAS_PREC_FP16_SPLIT 1  /* FP16 hi+lo operands on tensor cores, FP32 accumulation */
 #define FDAS_PREC_BF16_SPLIT 2  /* BF16 hi+lo operands on tensor cores, FP32 accumulation */
+#define FDAS_PREC_BF16_SPLIT3 3 /* BF16 hi+mid+lo operands on tensor cores, FP32 accumulation */
 
 /*
  * fdas_correlate_split -- fdas_correlate with the two radix-16 passes of
  * every forward and every inverse segment FFT done as matrix products on the
- * tensor cores (a9).  Section 4.2 writes the DFT as a product with the
+ * tensor cores (a9), for L = 2048 and 4096.  Section 4.2 writes the DFT as a product with the
  * Fourier matrix (Eq. matrixDFT) factorised into sparse stages
  * (Eq. CTfactorization); here one radix-16 stage over 32 segment columns is
  * the real product Y(32x32) = X(32x32) W(32x32) (re/im interleaved), each
@@ -349,11 +376,14 @@ int fdas_noise_means(const fdas_params *p, float *means, void *stream);
  * the template product and the powers stay FP32; `bank` is the FP32 bank of
  * fdas_make_templates.
  * prec: FDAS_PREC_FP32 (identical to fdas_correlate), FDAS_PREC_FP16_SPLIT
- *   (parts of 11 significant bits each, 22 together; an intermediate above
- *   65504 in magnitude overflows to inf) or FDAS_PREC_BF16_SPLIT (8 + 8 bits,
- *   FP32 range).
+ *   (parts of 11 significant bits each, 22 together; each DFT instance is
+ *   scaled by a power of two into FP16's range), FDAS_PREC_BF16_SPLIT (8 + 8
+ *   bits, FP32 range; its error exceeds 1e-3 of power at L >= 2048) or
+ *   FDAS_PREC_BF16_SPLIT3 (three BF16 parts, 8 + 8 + 8 bits, six products:
+ *   Xh Wh + Xh Wm + Xm Wh + Xh Wl + Xl Wh + Xm Wm).
  * Other arguments, layout and errors as fdas_correlate; FDAS_E_INVAL for any
- * other prec.
+ * other prec; FDAS_E_UNSUPPORTED for L = 1024 (its one-warp convolver has no
+ * split form) or interbin 2 with a split prec.
  */
 int fdas_correlate_split(const fdas_params *p, int32_t prec, const float *spec, int64_t nb,
                          const float *bank, float *plane, int64_t row_stride,

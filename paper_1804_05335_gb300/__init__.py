@@ -17,11 +17,12 @@ __all__ = [
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
+    "fdas_debug_wait_timeout",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
     "fdas_correlate_plane16", "FDAS_PLANE_F16", "FDAS_PLANE_BF16", "fdas_harmonic_sum",
     "fdas_harmonic_plan_bytes", "fdas_harmonic_plan", "fdas_harmonic_sum_planned", "FDAS_STATUS_BADPLAN",
     "fdas_noise_means",
-    "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT",
+    "FDAS_PREC_FP32", "FDAS_PREC_FP16_SPLIT", "FDAS_PREC_BF16_SPLIT", "FDAS_PREC_BF16_SPLIT3",
     "fdas_refine_fwd", "fdas_refine_bwd", "fdas_refine", "fdas_trial", "fdas_tuning",
     "fdas_batch_plan", "fdas_correlate_batched",
     "header_functions", "FDAS_CAND_PEAK", "FDAS_STATUS_OVERFLOW", "FDAS_STATUS_TIMEOUT",
@@ -50,6 +51,7 @@ FDAS_PLANE_BF16 = 2
 FDAS_PREC_FP32 = 0
 FDAS_PREC_FP16_SPLIT = 1
 FDAS_PREC_BF16_SPLIT = 2
+FDAS_PREC_BF16_SPLIT3 = 3
 
 c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
@@ -116,6 +118,8 @@ def load_library():
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_correlate_split": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
                                                 c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
+        "fdas_debug_wait_timeout": (ctypes.c_int, [P(fdas_params), c_vp, c_i64, c_vp, c_vp, c_i64,
+                                                   ctypes.c_uint32, c_vp, c_vp]),
         "fdas_correlate_plane16": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
                                                   c_i64, P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_harmonic_sum": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_i64, c_i32,
@@ -323,6 +327,14 @@ def fdas_correlate_split(p: fdas_params, prec: int, spec, nb: int, bank, plane, 
                                                _ptr(bank), _ptr(plane), int(row_stride), f,
                                                _ptr(status), _stream(stream)),
            "fdas_correlate_split")
+
+
+def fdas_debug_wait_timeout(p: fdas_params, spec, nb: int, bank, plane, row_stride: int,
+                            polls: int, status, stream=None) -> None:
+    _check(load_library().fdas_debug_wait_timeout(ctypes.byref(p), _ptr(spec), int(nb), _ptr(bank),
+                                                  _ptr(plane), int(row_stride), int(polls),
+                                                  _ptr(status), _stream(stream)),
+           "fdas_debug_wait_timeout")
 
 
 def fdas_threshold(plane, rows: int, width: int, row_stride: int, thr: float, want_flags: int,

@@ -251,6 +251,19 @@ int fdas_correlate(const fdas_params* p, const float* spec, int64_t nb, const fl
                             status, (cudaStream_t)stream);
 }
 
+int fdas_debug_wait_timeout(const fdas_params* p, const float* spec, int64_t nb, const float* bank,
+                            float* plane, int64_t row_stride, uint32_t polls, int32_t* status,
+                            void* stream) {
+    Grid g;
+    int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, nullptr, status);
+    if (rc != FDAS_OK) return rc;
+    if (!status || polls < 1 || polls > (1u << 24)) return FDAS_E_INVAL;
+    if (p->L != 1024 || p->interbin == 2) return FDAS_E_UNSUPPORTED;
+    return launch_wconv_wait_probe(p, g, reinterpret_cast<const float2*>(spec), nb,
+                                   reinterpret_cast<const float4*>(bank), plane, row_stride, polls,
+                                   status, (cudaStream_t)stream);
+}
+
 int fdas_correlate_plane16(const fdas_params* p, int32_t type, const float* spec, int64_t nb,
                            const float* bank, void* plane, int64_t row_stride,
                            const fdas_fused_threshold* fused, int32_t* status, void* stream) {
@@ -268,7 +281,8 @@ int fdas_correlate_plane16(const fdas_params* p, int32_t type, const float* spec
 int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, int64_t nb,
                          const float* bank, float* plane, int64_t row_stride,
                          const fdas_fused_threshold* fused, int32_t* status, void* stream) {
-    if (prec != FDAS_PREC_FP32 && prec != FDAS_PREC_FP16_SPLIT && prec != FDAS_PREC_BF16_SPLIT)
+    if (prec != FDAS_PREC_FP32 && prec != FDAS_PREC_FP16_SPLIT && prec != FDAS_PREC_BF16_SPLIT &&
+        prec != FDAS_PREC_BF16_SPLIT3)
         return FDAS_E_INVAL;
     Grid g;
     int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);

@@ -270,7 +270,12 @@ __global__ void __launch_bounds__(L / 16, L == 2048 ? 2 : 1) conv_kernel(const C
             }
         }
         if (__syncthreads_or(tmo)) {
-            if (t == 0 && A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
+            if (t == 0) {
+                if (A.status) atomicOr(A.status, FDAS_STATUS_TIMEOUT);
+                // the row's copy may still be in flight: wait for it (bounded)
+                // before the CTA's shared memory is released
+                mbar_wait_bounded(&hbar, hphase ^ 1u, kWaitLimit);
+            }
             break;
         }
 

@@ -35,6 +35,7 @@ int launch_correlate_split(const fdas_params* p, const Grid& g, int prec, const 
     switch (prec) {
         case FDAS_PREC_FP16_SPLIT: return dispatch_split<1>(p, a, fused != nullptr, st);
         case FDAS_PREC_BF16_SPLIT: return dispatch_split<2>(p, a, fused != nullptr, st);
+        case FDAS_PREC_BF16_SPLIT3: return dispatch_split<3>(p, a, fused != nullptr, st);
         default: return FDAS_E_INVAL;
     }
 }

@@ -6,8 +6,9 @@
 //
 // A complex value is a float2 (re, im) in an aligned register pair, so a
 // complex addition is one packed FADD2 (sm_100+), the same IEEE addition per
-// component.  Products by +-i cross the components and stay scalar, folded
-// into the additions that consume them.
+// component.  Products by +-i are folded into the additions that consume
+// them as packed additions of the swapped, sign-flipped pair (measured: fewer
+// instructions than two scalar additions).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -34,11 +35,11 @@ __device__ __forceinline__ float2 mul_si(float2 v) {
 // a + S i b  and  a - S i b
 template <int S>
 __device__ __forceinline__ float2 add_si(float2 a, float2 b) {
-    return S > 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+    return __fadd2_rn(a, S > 0 ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x));
 }
 template <int S>
 __device__ __forceinline__ float2 sub_si(float2 a, float2 b) {
-    return S > 0 ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
+    return __fadd2_rn(a, S > 0 ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x));
 }
 
 constexpr float kC8 = 0.92387953251128674f;  // cos(pi/8)

@@ -68,6 +68,11 @@ struct ConvArgs;
 // p->interbin == 2.
 int dispatch_wconv(const fdas_params* p, const ConvArgs& a, bool fused, bool batch, int out,
                    int ctas_per_sm, cudaStream_t st);
+// The L = 1024 convolver with its first template row's barrier armed and
+// no copy issued, `polls` polls per wait (fdas_debug_wait_timeout).
+int launch_wconv_wait_probe(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
+                            const float4* bank, float* plane, int64_t row_stride, uint32_t polls,
+                            int32_t* status, cudaStream_t st);
 // The convolver with half-bin sampling (interbin 2), convolve_interp2.cu.
 int dispatch_half_bins(const fdas_params* p, const ConvArgs& a, bool fused, bool batch,
                        int ctas_per_sm, cudaStream_t st);

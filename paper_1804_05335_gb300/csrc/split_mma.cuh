@@ -8,7 +8,11 @@
 // split into 16-bit hi + lo parts, x = x_hi + x_lo, W = W_hi + W_lo, and
 //   Y ~ X_hi W_hi + X_hi W_lo + X_lo W_hi
 // (the lo*lo term is below the FP32 accumulation error).  FP16 parts keep
-// ~22 significant bits, BF16 parts ~16.
+// ~22 significant bits, BF16 parts ~16.  PREC 3 splits both operands into
+// three BF16 parts (hi + mid + lo, ~24 significant bits) and keeps the six
+// products whose order is at most 2^-16 of the leading one:
+//   Y ~ Xh Wh + (Xh Wm + Xm Wh) + (Xh Wl + Xl Wh + Xm Wm),
+// dropping Xm Wl, Xl Wm and Xl Wl (order 2^-24 and below).
 //
 // FP16 has a narrow exponent range: a small operand's lo part would fall
 // into the subnormals and lose bits, a large one would overflow.  Each DFT
@@ -41,10 +45,12 @@ struct MmaLane {
     }
 };
 
-template <int PREC>   // 1 = FP16 hi+lo, 2 = BF16 hi+lo
+template <int PREC>   // 1 = FP16 hi+lo, 2 = BF16 hi+lo, 3 = BF16 hi+mid+lo
 struct SplitMMA {
+    static constexpr int NP = PREC == 3 ? 3 : 2;   // parts per operand
     uint32_t bh[2][4][2];   // [K step][N tile][reg] hi part of Wr
-    uint32_t bl[2][4][2];   // lo part
+    uint32_t bl[2][4][2];   // lo part (PREC 3: the middle part)
+    uint32_t bx[PREC == 3 ? 2 : 1][4][2];   // PREC 3: the lo part
 
     __device__ __forceinline__ static uint32_t pack(float a, float b) {
         if constexpr (PREC == 1) {
@@ -68,6 +74,17 @@ struct SplitMMA {
         const float2 h = unpack(hi);
         lo = pack(a - h.x, b - h.y);
     }
+    // hi, mid and lo packed pairs of (a, b): each part rounds the remainder
+    // of the parts before it
+    __device__ __forceinline__ static void split3(float a, float b, uint32_t& hi, uint32_t& mid,
+                                                  uint32_t& lo) {
+        hi = pack(a, b);
+        const float2 h = unpack(hi);
+        const float ra = a - h.x, rb = b - h.y;
+        mid = pack(ra, rb);
+        const float2 m = unpack(mid);
+        lo = pack(ra - m.x, rb - m.y);
+    }
 
     // S = -1 forward, +1 inverse
     template <int S>
@@ -87,7 +104,8 @@ struct SplitMMA {
                     // column n' = 2n (re out): (Re w, -Im w); n' = 2n+1 (im out): (Im w, Re w)
                     const float w0 = (g & 1) ? sn : cs;
                     const float w1 = (g & 1) ? cs : -sn;
-                    split(w0, w1, bh[s][j][r], bl[s][j][r]);
+                    if constexpr (PREC == 3) split3(w0, w1, bh[s][j][r], bl[s][j][r], bx[s][j][r]);
+                    else split(w0, w1, bh[s][j][r], bl[s][j][r]);
                 }
     }
 
@@ -149,16 +167,35 @@ struct SplitMMA {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 uint32_t ah[4], al[4];
-                // a0: row g, k = 8s+tig; a1: row g+8; a2: row g, k+4; a3: row g+8, k+4
-                split(x[2 * t][2 * s].x * s0, x[2 * t][2 * s].y * s0, ah[0], al[0]);
-                split(x[2 * t + 1][2 * s].x * s1, x[2 * t + 1][2 * s].y * s1, ah[1], al[1]);
-                split(x[2 * t][2 * s + 1].x * s0, x[2 * t][2 * s + 1].y * s0, ah[2], al[2]);
-                split(x[2 * t + 1][2 * s + 1].x * s1, x[2 * t + 1][2 * s + 1].y * s1, ah[3], al[3]);
+                if constexpr (PREC == 3) {
+                    uint32_t ax[4];   // lo parts; al holds the middle parts
+                    split3(x[2 * t][2 * s].x, x[2 * t][2 * s].y, ah[0], al[0], ax[0]);
+                    split3(x[2 * t + 1][2 * s].x, x[2 * t + 1][2 * s].y, ah[1], al[1], ax[1]);
+                    split3(x[2 * t][2 * s + 1].x, x[2 * t][2 * s + 1].y, ah[2], al[2], ax[2]);
+                    split3(x[2 * t + 1][2 * s + 1].x, x[2 * t + 1][2 * s + 1].y, ah[3], al[3],
+                           ax[3]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    mma(acc[j], ah, bh[s][j]);
-                    mma(acc[j], ah, bl[s][j]);
-                    mma(acc[j], al, bh[s][j]);
+                    for (int j = 0; j < 4; ++j) {   // smallest terms first
+                        mma(acc[j], ah, bx[s][j]);
+                        mma(acc[j], ax, bh[s][j]);
+                        mma(acc[j], al, bl[s][j]);
+                        mma(acc[j], ah, bl[s][j]);
+                        mma(acc[j], al, bh[s][j]);
+                        mma(acc[j], ah, bh[s][j]);
+                    }
+                } else {
+                    // a0: row g, k = 8s+tig; a1: row g+8; a2: row g, k+4; a3: row g+8, k+4
+                    split(x[2 * t][2 * s].x * s0, x[2 * t][2 * s].y * s0, ah[0], al[0]);
+                    split(x[2 * t + 1][2 * s].x * s1, x[2 * t + 1][2 * s].y * s1, ah[1], al[1]);
+                    split(x[2 * t][2 * s + 1].x * s0, x[2 * t][2 * s + 1].y * s0, ah[2], al[2]);
+                    split(x[2 * t + 1][2 * s + 1].x * s1, x[2 * t + 1][2 * s + 1].y * s1, ah[3],
+                          al[3]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        mma(acc[j], ah, bh[s][j]);
+                        mma(acc[j], ah, bl[s][j]);
+                        mma(acc[j], al, bh[s][j]);
+                    }
                 }
             }
             const float o0 = so[2 * t], o1 = so[2 * t + 1];

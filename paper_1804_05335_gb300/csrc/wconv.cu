@@ -39,4 +39,18 @@ int dispatch_wconv(const fdas_params* p, const ConvArgs& a, bool fused, bool bat
     }
 }
 
+int launch_wconv_wait_probe(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,
+                            const float4* bank, float* plane, int64_t row_stride, uint32_t polls,
+                            int32_t* status, cudaStream_t st) {
+    ConvArgs a = base_args(p, g, bank, nullptr, status);
+    a.spec = spec;
+    a.nb = nb;
+    a.plane = plane;
+    a.row_stride = row_stride;
+    a.items = series_items(g, p->L, positions(p, nb));
+    a.wait_limit = polls;
+    a.probe = 1;
+    return dispatch_wconv(p, a, false, false, 0, 0, st);
+}
+
 }  // namespace fdas

@@ -195,6 +195,48 @@ __device__ __forceinline__ void wstore2(void* row, int64_t i, float a, float b) 
         __stcs(reinterpret_cast<unsigned int*>(static_cast<uint16_t*>(row) + i), u);
     }
 }
+// The same stores, issued only where `ok` (one predicated instruction, no
+// branch): for the registers at a segment's edges.
+template <int OUT>
+__device__ __forceinline__ void wstore2_if(bool ok, void* row, int64_t i, float a, float b) {
+    if constexpr (OUT == 0) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+                     "@p st.global.cs.v2.f32 [%1], {%2, %3};\n\t}"
+                     ::"r"((int)ok), "l"(static_cast<float*>(row) + i), "f"(a), "f"(b) : "memory");
+    } else {
+        uint32_t u;
+        if constexpr (OUT == 1) {
+            __half2 h = __floats2half2_rn(a, b);
+            u = *reinterpret_cast<uint32_t*>(&h);
+        } else {
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            u = *reinterpret_cast<uint32_t*>(&h);
+        }
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+                     "@p st.global.cs.b32 [%1], %2;\n\t}"
+                     ::"r"((int)ok), "l"(static_cast<uint16_t*>(row) + i), "r"(u) : "memory");
+    }
+}
+template <int OUT>
+__device__ __forceinline__ void wstore1_if(bool ok, void* row, int64_t i, float a) {
+    if constexpr (OUT == 0) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+                     "@p st.global.cs.f32 [%1], %2;\n\t}"
+                     ::"r"((int)ok), "l"(static_cast<float*>(row) + i), "f"(a) : "memory");
+    } else {
+        uint16_t u;
+        if constexpr (OUT == 1) {
+            __half h = __float2half_rn(a);
+            u = *reinterpret_cast<uint16_t*>(&h);
+        } else {
+            __nv_bfloat16 h = __float2bfloat16_rn(a);
+            u = *reinterpret_cast<uint16_t*>(&h);
+        }
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+                     "@p st.global.cs.b16 [%1], %2;\n\t}"
+                     ::"r"((int)ok), "l"(static_cast<uint16_t*>(row) + i), "h"(u) : "memory");
+    }
+}
 template <int OUT>
 __device__ __forceinline__ void wstore1(void* row, int64_t i, float a) {
     if constexpr (OUT == 0) {
@@ -233,15 +275,15 @@ __device__ __forceinline__ float wepi_fast(const float2* v, int l, int ilo, int 
             xn.y = __shfl_sync(0xffffffffu, pv.y, (l + 1) & 31);
             const float2 d = x - xn;
             const float ph = kHalfBinScale * fmaf(d.x, d.x, d.y * d.y);
-            if (ok) {
-                wstore2<OUT>(prow, 2 * (rb + 32 * i), pf, ph);
-                mx = fmaxf(mx, fmaxf(pf, ph));
-            }
+            if constexpr (i >= 5 && i <= 26) wstore2<OUT>(prow, 2 * (rb + 32 * i), pf, ph);
+            else wstore2_if<OUT>(ok, prow, 2 * (rb + 32 * i), pf, ph);
+            // an edge register outside the segment can only cause a needless
+            // listing pass, which checks every position itself
+            mx = fmaxf(mx, fmaxf(pf, ph));
         } else {
-            if (ok) {
-                wstore1<OUT>(prow, rb + 32 * i, pf);
-                mx = fmaxf(mx, pf);
-            }
+            if constexpr (i >= 5 && i <= 26) wstore1<OUT>(prow, rb + 32 * i, pf);
+            else wstore1_if<OUT>(ok, prow, rb + 32 * i, pf);
+            mx = fmaxf(mx, pf);
         }
     });
     return mx;

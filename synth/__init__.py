@@ -124,11 +124,11 @@ WORKLOADS = {
     # [1e4, 4e6], z in [-200, 200], S/N 6-20; z = -200..200 step 2
     # (201 templates), taps padded to 256; segment length swept 1024-4096.
     "production": Workload("production", 1 << 23, 2, _production_injections(2),
-                           -200, 200, 2, 256, 2048),
+                           -200, 200, 2, 256, 1024),
     # The production search on a 2^20-sample series (201 x 2^20 plane, 0.84 GB):
     # same kernels and launch shapes, small enough for hardware-counter captures.
     "medium": Workload("medium", 1 << 20, 3, _production_injections(3, rmax=5.0e5),
-                       -200, 200, 2, 256, 2048),
+                       -200, 200, 2, 256, 1024),
     # A few-second oracle case that still spans several segments and a
     # ragged tail: 2^14 samples, 8192 bins, 1024-point segments of 960
     # useful bins (8.53 segments).

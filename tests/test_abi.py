@@ -79,7 +79,7 @@ def test_invalid_buffers_rejected_before_launch():
         lambda: F.fdas_threshold(256, 0, 10, 10, 20.0, 0, 256, 4, 256, stream=0),  # rows
         lambda: F.fdas_threshold(256, 3, 10, 9, 20.0, 0, 256, 4, 256, stream=0),   # stride
         lambda: F.fdas_threshold(256, 3, 10, 10, 20.0, 4, 256, 4, 256, stream=0),  # flags
-        lambda: F.fdas_correlate_split(p, 3, 256, 1000, 256, 256, 2000, stream=0),    # prec
+        lambda: F.fdas_correlate_split(p, 4, 256, 1000, 256, 256, 2000, stream=0),    # prec
         lambda: F.fdas_correlate_split(p, -1, 256, 1000, 256, 256, 2000, stream=0),   # prec
         lambda: F.fdas_correlate_split(p, 1, 0, 1000, 256, 256, 2000, stream=0),      # NULL spec
         lambda: F.fdas_correlate_split(p, 2, 256, 1000, 256, 256, 2002, stream=0),    # stride % 4

@@ -99,3 +99,53 @@ def test_autotune_picks_a_candidate(F, tmp_path):
     again = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=((1024, 0), (2048, 0), (2048, 1)),
                      cache_path=path)
     assert again == res
+
+
+@pytest.mark.parametrize("L", [1024, 2048])
+def test_batched_production_bank(F, L):
+    """The production template bank (z = -200..200 step 2, M = 256: four
+    template groups of increasing overlap) in the batched launch, with one CTA
+    per SM so that each CTA's range crosses trial and group boundaries, and a
+    pool small enough for several waves: every trial's spectrum, plane and
+    candidate list are bit-identical to the single-series call, and a trial
+    that is not the first of its wave matches the FP64 oracle."""
+    from paper_1804_05335_gb300.batch import BatchSearch
+    from paper_1804_05335_gb300.search import Search
+    ns = [1 << 13, 1 << 15, 1 << 14, 1 << 16, 1 << 13, 1 << 14]
+    bs = BatchSearch(ns, L, 256, -200, 200, 2, thr=20.0, pool_bytes=64 << 20, ctas_per_sm=1)
+    assert len(bs.waves) > 1
+    assert len(F.fdas_template_groups(bs.p)) == 4
+    xs = [synth.make_series(n, ((n / 5 + 0.3, 150.0, 20.0), (n / 3 + 0.7, -120.0, 15.0)), 400 + i)
+          for i, n in enumerate(ns)]
+    for i, x in enumerate(xs):
+        bs.set_series(i, x)
+    bs.front(stream=None)
+    planes = {}
+    for k, w in enumerate(bs.waves):
+        bs.correlate_wave(k)
+        torch.cuda.synchronize()
+        for i in w:
+            planes[i] = bs.plane_of(i).cpu().numpy().copy()
+    cands, counts = bs.candidates()
+    assert bs.status.item() == 0
+    for i, n in enumerate(ns):
+        S = Search(n, L, 256, -200, 200, 2, thr=20.0)
+        S.series.copy_(torch.from_numpy(xs[i]))
+        S.step()
+        torch.cuda.synchronize()
+        assert np.array_equal(S.spec.cpu().numpy(), bs.spec_of(i).cpu().numpy())
+        assert np.array_equal(S.plane2d().cpu().numpy(), planes[i]), i
+        r, c, p, fl, total = S.candidates()
+        br, bc, bp = cands[i]
+        assert total > 0
+        assert np.array_equal(r, br) and np.array_equal(c, bc) and np.array_equal(p, bp)
+    # a later trial of a wave, on the oracle's own spectrum, against the oracle
+    k = next(k for k, w in enumerate(bs.waves) if len(w) > 1)
+    i = bs.waves[k][-1]
+    A = O.normalise(O.real_spectrum(xs[i]), 1024)
+    bs.spec_of(i).copy_(torch.from_numpy(A.astype(np.complex64)))
+    bs.correlate_wave(k)
+    torch.cuda.synchronize()
+    ref = O.plane(A.astype(np.complex64).astype(np.complex128), O.z_grid(-200, 200, 2))
+    err = np.abs(bs.plane_of(i).cpu().numpy().astype(np.float64) - ref)
+    assert err.max() < 1e-3, (i, err.max())

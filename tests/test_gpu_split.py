@@ -4,14 +4,20 @@ against the FP32 form on the same spectrum.
 
 Tolerances on normalised power (noise mean 1), |P_gpu - P_ref| <= a + b P_ref:
   FP32 through this entry: bit-identical to fdas_correlate.
-  FP16 hi+lo (22-bit operand pairs, per-instance power-of-two scaling):
-      a = 1e-3, b = 0 (the FP32 bar).
-  BF16 hi+lo (16-bit operand pairs): each operand carries a relative error
-      of at most u = 2^-16 and the lo*lo term drops another u, so one DFT
-      stage loses at most ~3u in amplitude; four stages give 12u and the
-      power twice that, b = 24 * 2^-16 ~ 3.7e-4, plus the FP32 bar a = 1e-3.
+  FP16 hi+lo (22-bit operand pairs, per-instance power-of-two scaling) and
+  BF16 hi+mid+lo (24-bit operand triples, six products): a = 1e-3, b = 0,
+      the task's bar for every form.
+  BF16 hi+lo (16-bit operand pairs) does NOT meet that bar at L >= 2048 and
+      is outside the accuracy claim; it is held only to its own derived bound:
+      each operand carries a relative error of at most u = 2^-16 and the
+      lo*lo term drops another u, so one DFT stage loses at most ~3u in
+      amplitude; four stages give 12u and the power twice that,
+      b = 24 * 2^-16 ~ 3.7e-4, plus a = 1e-3.
 Inputs are seeded synthetic series; no expected value comes from the GPU.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -21,8 +27,9 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {1: (1e-3, 0.0), 2: (1e-3, 24 * 2.0 ** -16)}
-NAMES = {1: "fp16", 2: "bf16"}
+TOL = {1: (1e-3, 0.0), 2: (1e-3, 24 * 2.0 ** -16), 3: (1e-3, 0.0)}
+NAMES = {1: "fp16", 2: "bf16", 3: "bf16x3"}
+PRECS = pytest.mark.parametrize("prec", [1, 2, 3], ids=["fp16", "bf16", "bf16x3"])
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +63,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", [1, 2], ids=["fp16", "bf16"])
+@PRECS
 @pytest.mark.parametrize("n,L,M,zmin,zmax,zstep,ib", CASES)
 def test_split_plane_matches_oracle(F, prec, n, L, M, zmin, zmax, zstep, ib):
     x = synth.make_series(n, ((n / 7 + 0.25, 6.0, 18.0), (n / 3, -14.0, 20.0)), 9)
@@ -76,7 +83,7 @@ def test_split_rejects_warp_segment_length(F):
     """L = 1024 runs the one-warp-per-segment convolver, which has no split form."""
     S = _search(n=1 << 14, L=1024, M=64, zmin=-20, zmax=20, zstep=2)
     S.make_templates()
-    for prec in (1, 2):
+    for prec in (1, 2, 3):
         with pytest.raises(F.FdasError) as e:
             S.correlate(fused=False, prec=prec)
         assert e.value.code == F.FDAS_E_UNSUPPORTED
@@ -96,7 +103,7 @@ def test_split_fp32_entry_is_fdas_correlate(F):
     assert torch.equal(a, S.plane)
 
 
-@pytest.mark.parametrize("prec", [1, 2], ids=["fp16", "bf16"])
+@PRECS
 def test_split_tiny_and_odd_spectra(F, prec):
     for nb in (1, 5, 999, 1793):
         A = synth.random_spectrum(nb, 40 + nb)
@@ -135,41 +142,72 @@ def test_fp16_split_keeps_range_on_strong_lines(F):
     assert err.max() < 1e-5 * ref.max(), (err.max(), ref.max())
 
 
-@pytest.mark.parametrize("prec", [1, 2], ids=["fp16", "bf16"])
-def test_split_production_sampled_and_candidates(F, prec):
-    """2^23-sample series, zmax = 200, L = 2048: sampled windows against the
-    oracle, and the fused candidate list against the FP32 form's."""
+def _production_windows(wl):
+    rng = np.random.default_rng(2048)
+    starts = list(rng.integers(0, wl.nb - 256, 8)) + [0, wl.nb - 256]
+    return starts + [int(r0) - 128 for r0, _, _ in wl.injections]
+
+
+def test_split_production_error_table(F):
+    """2^23-sample series, zmax = 200, at L = 2048 and 4096: every form's
+    power error against the FP64 oracle on 18 windows of 256 bins (8 random,
+    both ends, every injection) over all 201 rows, and its fused candidate
+    list against the FP32 form's.  FP32, FP16 hi+lo and BF16 hi+mid+lo must
+    hold 1e-3; BF16 hi+lo is reported and held to its derived bound only.
+    With FDAS_SPLIT_TABLE set, the table is written there as JSON."""
     wl = synth.workload("production")
     x = wl.series()
     A = O.normalise(O.real_spectrum(x), wl.median_block).astype(np.complex64)
     A64 = A.astype(np.complex128)
-    S = _search(n=wl.n, L=2048, M=wl.M, zmin=wl.zmin, zmax=wl.zmax, zstep=wl.zstep,
-                thr=wl.threshold, cap=1 << 16)
-    S.spec.copy_(torch.from_numpy(A))
-    S.make_templates()
-    S.status.zero_()
-    S.correlate(fused=True)
-    r0_, c0_, p0_, _, tot0 = S.candidates()
-    S.correlate(fused=True, prec=prec)
-    r1_, c1_, p1_, _, tot1 = S.candidates()
-    assert S.status.item() == 0
-    plane = S.plane2d()
     zs = O.z_grid(wl.zmin, wl.zmax, wl.zstep)
-    rng = np.random.default_rng(2048)
-    starts = list(rng.integers(0, wl.nb - 256, 6)) + [0, wl.nb - 256]
-    starts += [int(r0) - 128 for r0, _, _ in wl.injections]
-    for r0 in starts:
-        got = plane[:, 2 * r0: 2 * (r0 + 256)].cpu().numpy().astype(np.float64)
-        ref = O.plane_window(A64, zs, r0, 256)
-        ok, emax = _within(got, ref, prec)
-        assert ok, (r0, emax)
-    # candidates: the same list as the FP32 form except within tolerance of
-    # the threshold, and powers within tolerance of each other
-    a, b = TOL[prec]
-    g = {(int(r), int(c)): float(p) for r, c, p in zip(r1_, c1_, p1_)}
-    f = {(int(r), int(c)): float(p) for r, c, p in zip(r0_, c0_, p0_)}
-    for key in set(g) ^ set(f):
-        v = g.get(key, f.get(key))
-        assert abs(v - wl.threshold) <= a + b * wl.threshold, key
-    for key in set(g) & set(f):
-        assert abs(g[key] - f[key]) <= a + b * f[key], key
+    starts = _production_windows(wl)
+    refs = {r0: O.plane_window(A64, zs, r0, 256) for r0 in starts}
+    table = {}
+    for L in (2048, 4096):
+        S = _search(n=wl.n, L=L, M=wl.M, zmin=wl.zmin, zmax=wl.zmax, zstep=wl.zstep,
+                    thr=wl.threshold, cap=1 << 16)
+        S.spec.copy_(torch.from_numpy(A))
+        S.make_templates()
+        cands = {}
+        for prec in (0, 1, 2, 3):
+            S.status.zero_()
+            S.correlate(fused=True, prec=prec)
+            r, c, p, _, tot = S.candidates()
+            assert S.status.item() == 0
+            cands[prec] = {(int(a), int(b)): float(v) for a, b, v in zip(r, c, p)}
+            plane = S.plane2d()
+            errs, big = [], []
+            for r0 in starts:
+                got = plane[:, 2 * r0: 2 * (r0 + 256)].cpu().numpy().astype(np.float64)
+                e = np.abs(got - refs[r0])
+                errs.append(e.ravel())
+                big.append((e / np.maximum(refs[r0], 1e-30))[refs[r0] > 20.0])
+            e = np.concatenate(errs)
+            rel = np.concatenate(big)
+            name = "fp32" if prec == 0 else NAMES[prec]
+            # candidate lists against the FP32 form: symmetric difference, and
+            # the largest power difference on the common points
+            f = cands[0]
+            g = cands[prec]
+            common = set(f) & set(g)
+            dpow = max((abs(g[k] - f[k]) for k in common), default=0.0)
+            table["L%d_%s" % (L, name)] = {
+                "max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
+                "max_rel_above_20": float(rel.max()) if rel.size else None,
+                "points": int(e.size), "candidates": len(g),
+                "cand_only_here": len(set(g) - set(f)), "cand_only_fp32": len(set(f) - set(g)),
+                "cand_max_power_diff": dpow}
+            a, b = TOL.get(prec, (1e-3, 0.0))
+            for key in set(g) ^ set(f):
+                v = g.get(key, f.get(key))
+                assert abs(v - wl.threshold) <= a + b * wl.threshold, (name, L, key)
+    out = os.environ.get("FDAS_SPLIT_TABLE")
+    if out:
+        with open(out, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+    for L in (2048, 4096):
+        for name in ("fp32", "fp16", "bf16x3"):
+            assert table["L%d_%s" % (L, name)]["max_abs"] < 1e-3, (L, name, table)
+        # the two-part BF16 form: its own bound only (a known miss of 1e-3)
+        t = table["L%d_bf16" % L]
+        assert t["max_abs"] < 1e-3 + 24 * 2.0 ** -16 * 500.0, (L, t)
