@@ -285,18 +285,20 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- scope rows
 def batched_row(args, torch, dev):
-    """256 dispersion trials of uneven length (2^20..2^23 samples, log-uniform
-    over the FFT sizes), 0-2 injections each; autotuned, graph-captured."""
+    """256 dispersion trials of uneven length, log-uniform in [2^20, 2^23]
+    samples (rounded to even), 0-2 injections each; autotuned,
+    graph-captured."""
     from paper_1804_05335_gb300.autotune import autotune
     from paper_1804_05335_gb300.batch import BatchSearch
     rng = np.random.default_rng(3)
     ntr = args.batch_trials
-    ns = [1 << int(p) for p in rng.integers(20, 24, ntr)]
+    ns = [2 * int(round(2.0 ** float(e))) for e in rng.uniform(19.0, 22.0, ntr)]
     probe = ns[:8]
     t0 = time.perf_counter()
     tune = autotune(probe, 256, -200, 200, 2, use_cache=False)
     t_tune = time.perf_counter() - t0
     bs = BatchSearch(ns, tune["L"], 256, -200, 200, 2, thr=20.0, ctas_per_sm=tune["ctas_per_sm"],
+                     templates_per_block=tune["templates_per_block"],
                      pool_bytes=48 << 30, cap_per_wave=1 << 16, device=dev)
     host = []
     for i, n in enumerate(ns):
@@ -316,7 +318,12 @@ def batched_row(args, torch, dev):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     cands, counts = bs.candidates()
-    return {"trials": ntr, "sizes": {str(k): int(v) for k, v in zip(*np.unique(ns, return_counts=True))},
+    na = np.asarray(ns)
+    pow2 = int(np.sum((na & (na - 1)) == 0))
+    return {"trials": ntr,
+            "sizes": {"min": int(na.min()), "median": int(np.median(na)), "max": int(na.max()),
+                      "log2_quartiles": [float(v) for v in np.percentile(np.log2(na), [25, 50, 75])],
+                      "powers_of_two": pow2, "total_samples": int(na.sum())},
             "waves": len(bs.waves), "plane_points": bs.plane_points,
             "ms_per_batch": ms, "points_per_s": bs.plane_points / (ms / 1e3),
             "candidates": int(sum(len(v[0]) for v in cands.values())),

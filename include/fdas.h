@@ -406,6 +406,11 @@ typedef struct {
 /* Launch tuning (NULL or 0 fields = defaults). */
 typedef struct {
     int32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = the occupancy maximum */
+    int32_t templates_per_block;  /* L = 1024: templates a CTA applies to a segment
+                                   * before the next segment (the work order within
+                                   * a template group); 0 = the whole group, so one
+                                   * forward FFT per segment serves every template.
+                                   * Ignored for L = 2048, 4096. */
 } fdas_tuning;
 
 /*

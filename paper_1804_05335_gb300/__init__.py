@@ -75,7 +75,7 @@ class fdas_trial(ctypes.Structure):
 
 
 class fdas_tuning(ctypes.Structure):
-    _fields_ = [("ctas_per_sm", c_i32)]
+    _fields_ = [("ctas_per_sm", c_i32), ("templates_per_block", c_i32)]
 
 
 class FdasError(RuntimeError):
@@ -374,9 +374,9 @@ def fdas_batch_plan(p: fdas_params, trials) -> int:
 
 def fdas_correlate_batched(p: fdas_params, trials_dev, ntrials: int, total_items: int, bank,
                            fused: fdas_fused_threshold | None = None, ctas_per_sm: int = 0,
-                           status=None, stream=None) -> None:
+                           status=None, stream=None, templates_per_block: int = 0) -> None:
     f = ctypes.byref(fused) if fused is not None else None
-    tun = fdas_tuning(int(ctas_per_sm))
+    tun = fdas_tuning(int(ctas_per_sm), int(templates_per_block))
     _check(load_library().fdas_correlate_batched(ctypes.byref(p), _ptr(trials_dev), int(ntrials),
                                                  int(total_items), _ptr(bank), f,
                                                  ctypes.byref(tun), _ptr(status),

@@ -22,7 +22,8 @@ from . import (fdas_bank_floats, fdas_batch_plan, fdas_correlate_batched, fdas_f
 class BatchSearch:
     def __init__(self, ns, L: int, M: int, zmin: int, zmax: int, zstep: int, interbin: int = 1,
                  median_block: int = 1024, thr: float = 20.0, cap_per_wave: int = 1 << 16,
-                 pool_bytes: int = 32 << 30, ctas_per_sm: int = 0, device="cuda"):
+                 pool_bytes: int = 32 << 30, ctas_per_sm: int = 0, templates_per_block: int = 0,
+                 device="cuda"):
         self.ns = [int(n) for n in ns]
         self.p = params(L, M, zmin, zmax, zstep, interbin)
         self.K = fdas_num_templates(self.p)
@@ -30,6 +31,7 @@ class BatchSearch:
         self.median_block = int(median_block)
         self.thr = float(thr)
         self.ctas_per_sm = int(ctas_per_sm)
+        self.templates_per_block = int(templates_per_block)
         dev = torch.device(device)
         self.device = dev
         nbs = [n // 2 for n in self.ns]
@@ -110,7 +112,7 @@ class BatchSearch:
     def correlate_wave(self, k: int, stream=None) -> None:
         fdas_correlate_batched(self.p, self.wave_tables[k], len(self.waves[k]),
                                self.wave_items[k], self.bank, self.fused[k], self.ctas_per_sm,
-                               self.status, stream)
+                               self.status, stream, self.templates_per_block)
 
     def run(self, stream=None) -> None:
         self.front(stream)

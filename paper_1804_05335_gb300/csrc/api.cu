@@ -143,7 +143,7 @@ int64_t series_items(const Grid& g, int L, int64_t npos) {
     for (int k = 0; k < g.ng; ++k) {
         const int64_t B = L - g.gM[k];
         const int64_t segs = (npos + B - 1) / B;
-        items += (L == 1024 ? (segs + 3) / 4 : segs) * g.gK[k];
+        items += (L == 1024 ? (segs + kWarpSegments - 1) / kWarpSegments : segs) * g.gK[k];
     }
     return items;
 }
@@ -330,10 +330,11 @@ int fdas_correlate_batched(const fdas_params* p, const fdas_trial* trials, int32
     }
     if (status && !aligned(status, 4)) return FDAS_E_INVAL;
     const int cps = tuning ? tuning->ctas_per_sm : 0;
-    if (cps < 0) return FDAS_E_INVAL;
+    const int tpb = tuning ? tuning->templates_per_block : 0;
+    if (cps < 0 || tpb < 0) return FDAS_E_INVAL;
     return launch_correlate_batched(p, g, trials, ntrials, total_items,
-                                    reinterpret_cast<const float4*>(bank), fused, cps, status,
-                                    (cudaStream_t)stream);
+                                    reinterpret_cast<const float4*>(bank), fused, cps, tpb,
+                                    status, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -40,6 +40,7 @@ struct ConvArgs {
     int32_t ng;
     uint32_t wait_limit;   // polls of a bounded wait before it gives up (0: kWaitLimit)
     int32_t probe;         // diagnostic (L = 1024): arm the first row's barrier, issue no copy
+    int32_t tpb;           // L = 1024: templates per chunk of a group's unit order (0: all)
     int32_t gM[kMaxGroups];
     int32_t gb0[kMaxGroups];
     int32_t gK[kMaxGroups];
@@ -207,6 +208,7 @@ inline ConvArgs base_args(const fdas_params* p, const Grid& g, const float4* ban
     a.ntrials = 0;
     a.wait_limit = 0;
     a.probe = 0;
+    a.tpb = 0;
     return a;
 }
 

@@ -39,9 +39,10 @@ int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, in
 
 int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_trial* trials,
                              int32_t ntrials, int64_t total_items, const float4* bank,
-                             const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
-                             cudaStream_t st) {
+                             const fdas_fused_threshold* fused, int ctas_per_sm, int tpb,
+                             int32_t* status, cudaStream_t st) {
     ConvArgs a = base_args(p, g, bank, fused, status);
+    a.tpb = tpb;
     a.trials = trials;
     a.ntrials = ntrials;
     a.items = total_items;

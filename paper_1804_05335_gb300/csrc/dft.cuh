@@ -8,7 +8,8 @@
 // complex addition is one packed FADD2 (sm_100+), the same IEEE addition per
 // component.  Products by +-i are folded into the additions that consume
 // them as packed additions of the swapped, sign-flipped pair (measured: fewer
-// instructions than two scalar additions).
+// instructions than two scalar additions), and products by constant
+// twiddles are two packed operations (cmul_k).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -46,6 +47,13 @@ constexpr float kC8 = 0.92387953251128674f;  // cos(pi/8)
 constexpr float kS8 = 0.38268343236508978f;  // sin(pi/8)
 constexpr float kR2 = 0.70710678118654752f;  // 1/sqrt(2)
 
+// v * (c + i s) for compile-time c, s as two packed operations:
+// (v.x c, v.y c) + (v.y, v.x) (-s, s)  (the swapped pair is an operand form of
+// the packed multiply-add, no extra instruction)
+__device__ __forceinline__ float2 cmul_k(float2 v, float c, float s) {
+    return __ffma2_rn(make_float2(v.y, v.x), make_float2(-s, s), __fmul2_rn(v, make_float2(c, c)));
+}
+
 // v * w16^m,  w16 = exp(S i 2 pi / 16),  m a compile-time constant
 template <int S, int MM>
 __device__ __forceinline__ float2 w16(float2 v) {
@@ -60,21 +68,20 @@ __device__ __forceinline__ float2 w16(float2 v) {
     } else if constexpr (m == 12) {
         return mul_si<-S>(v);
     } else if constexpr (m == 2) {            // (1 + S i)/sqrt2
-        return make_float2((v.x - sg * v.y) * kR2, (v.y + sg * v.x) * kR2);
+        return __fmul2_rn(add_si<S>(v, v), make_float2(kR2, kR2));
     } else if constexpr (m == 6) {            // (-1 + S i)/sqrt2
-        return make_float2((-v.x - sg * v.y) * kR2, (-v.y + sg * v.x) * kR2);
+        return __fmul2_rn(sub_si<S>(v, v), make_float2(-kR2, -kR2));
     } else if constexpr (m == 10) {           // (-1 - S i)/sqrt2
-        return make_float2((-v.x + sg * v.y) * kR2, (-v.y - sg * v.x) * kR2);
+        return __fmul2_rn(add_si<S>(v, v), make_float2(-kR2, -kR2));
     } else if constexpr (m == 14) {           // (1 - S i)/sqrt2
-        return make_float2((v.x + sg * v.y) * kR2, (v.y - sg * v.x) * kR2);
+        return __fmul2_rn(sub_si<S>(v, v), make_float2(kR2, kR2));
     } else {
         // odd m: cos/sin of 2 pi m/16 from the two octant constants
         constexpr float c = (m == 1 || m == 15) ? kC8 : (m == 3 || m == 13) ? kS8
                           : (m == 5 || m == 11) ? -kS8 : -kC8;
         constexpr float s0 = (m == 1 || m == 7) ? kS8 : (m == 3 || m == 5) ? kC8
                            : (m == 9 || m == 15) ? -kS8 : -kC8;
-        constexpr float s = sg * s0;
-        return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
+        return cmul_k(v, c, sg * s0);
     }
 }
 
@@ -192,7 +199,7 @@ __device__ __forceinline__ float2 w32(float2 v) {
         return w16<S, K / 2>(v);
     } else {
         constexpr float c = kW32c[K], s = (float)S * kW32s[K];
-        return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
+        return cmul_k(v, c, s);
     }
 }
 

@@ -17,8 +17,19 @@
 //   O = (Z_k - conj Z_{N-k}) / 2i,   X_0 := 0,
 // selects the lower median of |X_k|^2 in the block exactly (radix select on
 // the float bit patterns) and scales the block by sqrt(ln 2 / median).
+//
+// A series whose length n is even but not a power of two takes the N-point
+// DFT (N = n/2) by Bluestein's chirp-z identity: with c_m = exp(-i pi m^2/N),
+//   Z_k = sum_m z_m exp(-i 2 pi m k / N) = c_k sum_m (z_m c_m) conj(c_{k-m}),
+// a linear convolution evaluated as a circular one of power-of-two length
+// P >= 2N - 1 with the three-pass FFT above: A = FFT(z c), B = FFT(conj c
+// placed circularly), D = FFT(conj(A B)), and Z_k = c_k conj(D_k) / P (the
+// inverse by conjugation).  m^2 is reduced modulo 2N in integers before the
+// FP32 sine and cosine, so the chirp's phase error stays at the rounding of
+// (m^2 mod 2N)/N.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "dft.cuh"
@@ -230,10 +241,33 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
     return prefix;
 }
 
+// c_m = exp(-i pi m^2 / N) for 0 <= m < 2^24: m^2 mod 2N in integers, then FP32
+__device__ __forceinline__ float2 chirp(int64_t m, int64_t N) {
+    const int64_t r = (m * m) % (2 * N);
+    float s, c;
+    sincospif((float)r / (float)N, &s, &c);
+    return make_float2(c, -s);
+}
+
+// Z_k of the N-point DFT from the FFT output D: Z = D (power-of-two N) or,
+// after Bluestein's convolution of length P, Z_k = c_k conj(D_k) / P.
+template <bool BLUE>
+__device__ __forceinline__ float2 z_value(const float2* __restrict__ D, int64_t k, int64_t N,
+                                          float inv_p) {
+    const float2 d = D[k];
+    if constexpr (!BLUE) {
+        return d;
+    } else {
+        const float2 c = chirp(k, N);
+        return make_float2(inv_p * fmaf(c.x, d.x, c.y * d.y), inv_p * fmaf(c.y, d.x, -c.x * d.y));
+    }
+}
+
 // one CTA per median block: real-spectrum post-processing + normalisation
+template <bool BLUE>
 __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__ Z,
                                                       float2* __restrict__ spec, int64_t N,
-                                                      int block) {
+                                                      int block, float inv_p) {
     extern __shared__ float2 psm[];
     float2* xs = psm;
     uint32_t* keys = reinterpret_cast<uint32_t*>(xs + block);
@@ -244,8 +278,8 @@ __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__
     const int64_t n = 2 * N;
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const int64_t k = k0 + i;
-        const float2 zk = Z[k];
-        const float2 zm = Z[(N - k) & (N - 1)];
+        const float2 zk = z_value<BLUE>(Z, k, N, inv_p);
+        const float2 zm = z_value<BLUE>(Z, k == 0 ? 0 : N - k, N, inv_p);
         const float ex = 0.5f * (zk.x + zm.x), ey = 0.5f * (zk.y - zm.y);
         const float ox = 0.5f * (zk.y + zm.y), oy = -0.5f * (zk.x - zm.x);
         float s, c;
@@ -266,10 +300,85 @@ __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__
     }
 }
 
+// Bluestein inputs: a[m] = z_m c_m for m < N, 0 up to P
+__global__ void __launch_bounds__(kFeThreads) bs_chirp_in(const float2* __restrict__ z,
+                                                          float2* __restrict__ a, int64_t N,
+                                                          int64_t P) {
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < P;
+         m += (int64_t)gridDim.x * blockDim.x)
+        a[m] = m < N ? c_mul(z[m], chirp(m, N)) : make_float2(0.f, 0.f);
+}
+
+// the convolution kernel conj(c_j), j in (-N, N), placed circularly in P
+__global__ void __launch_bounds__(kFeThreads) bs_chirp_kernel(float2* __restrict__ b, int64_t N,
+                                                              int64_t P) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = j < N ? j : (j > P - N ? P - j : -1);
+        const float2 c = d >= 0 ? chirp(d, N) : make_float2(0.f, 0.f);
+        b[j] = make_float2(c.x, -c.y);
+    }
+}
+
+// x = conj(x y): the product of the two spectra, conjugated so that a forward
+// FFT of it gives the conjugated inverse
+__global__ void __launch_bounds__(kFeThreads) bs_mul_conj(float2* __restrict__ x,
+                                                          const float2* __restrict__ y,
+                                                          int64_t P) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float2 p = c_mul(x[k], y[k]);
+        x[k] = make_float2(p.x, -p.y);
+    }
+}
+
 static int log2i(int64_t v) {
     int p = 0;
     while (((int64_t)1 << p) < v) ++p;
     return p;
+}
+
+// Bluestein convolution length for a series of n samples (n even, not a
+// power of two): the least power of two >= n - 1 = 2N - 1; 0 if out of range.
+static int64_t bluestein_length(int64_t n) {
+    if (n < (1 << 13) || n > ((int64_t)1 << 24) || (n & 1) || !(n & (n - 1))) return 0;
+    int64_t P = 1;
+    while (P < n - 1) P <<= 1;
+    return P;
+}
+
+// The three-pass forward FFT of P points (a power of two, 2^12..2^24): in ->
+// out (natural order; out may be in), tmp holds P values in between.
+static int fft_pow2(const float2* in, float2* tmp, float2* out, int64_t P, cudaStream_t st) {
+    const int p = log2i(P);
+    const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
+    const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
+    const int64_t N12 = (int64_t)N1 * N2;
+    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(in, tmp, N3, N12, P);
+    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(tmp, N1, N2);
+    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(tmp, out, N1, N2,
+                                                                             N3);
+    return cuda_status(cudaGetLastError());
+}
+
+static int frontend_setup() {
+    const size_t tile_sm = tile_bytes(256);   // the largest line (attribute)
+    const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
+    int rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a), tile_sm, kFeThreads, nullptr,
+                          nullptr);
+    if (rc == FDAS_OK)
+        rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b), tile_sm, kFeThreads, nullptr,
+                          nullptr);
+    if (rc == FDAS_OK)
+        rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c), tile_sm, kFeThreads, nullptr,
+                          nullptr);
+    if (rc == FDAS_OK)
+        rc = kernel_setup(reinterpret_cast<const void*>(&fe_post<false>), post_max, kFeThreads,
+                          nullptr, nullptr);
+    if (rc == FDAS_OK)
+        rc = kernel_setup(reinterpret_cast<const void*>(&fe_post<true>), post_max, kFeThreads,
+                          nullptr, nullptr);
+    return rc;
 }
 
 }  // namespace fdas
@@ -279,8 +388,10 @@ using namespace fdas;
 extern "C" {
 
 size_t fdas_normalise_workspace_bytes(int64_t n) {
-    if (n < (1 << 13) || n > ((int64_t)1 << 25) || (n & (n - 1))) return 0;
-    return (size_t)(n / 2) * sizeof(float2);
+    if (n >= (1 << 13) && n <= ((int64_t)1 << 25) && !(n & (n - 1)))
+        return (size_t)(n / 2) * sizeof(float2);
+    const int64_t P = bluestein_length(n);
+    return P ? (size_t)(3 * P) * sizeof(float2) : 0;
 }
 
 int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* spec, void* work,
@@ -292,35 +403,41 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     if (!aligned(series, 8) || !aligned(spec, 8) || !aligned(work, 16)) return FDAS_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = n / 2;
-    const int p = log2i(N);
-    const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
-    const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
-    const int64_t N12 = (int64_t)N1 * N2;
-    const size_t tile_sm = tile_bytes(256);   // the largest line (attribute)
-    {
-        const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
-        int rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a), tile_sm, kFeThreads,
-                              nullptr, nullptr);
-        if (rc == FDAS_OK)
-            rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b), tile_sm, kFeThreads,
-                              nullptr, nullptr);
-        if (rc == FDAS_OK)
-            rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c), tile_sm, kFeThreads,
-                              nullptr, nullptr);
-        if (rc == FDAS_OK)
-            rc = kernel_setup(reinterpret_cast<const void*>(&fe_post), post_max, kFeThreads,
-                              nullptr, nullptr);
-        if (rc != FDAS_OK) return rc;
-    }
+    int rc = frontend_setup();
+    if (rc != FDAS_OK) return rc;
     float2* sp = reinterpret_cast<float2*>(spec);
     float2* wk = reinterpret_cast<float2*>(work);
-    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(
-        reinterpret_cast<const float2*>(series), sp, N3, N12, N);
-    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(sp, N1, N2);
-    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(sp, wk, N1, N2, N3);
+    const float2* z = reinterpret_cast<const float2*>(series);
     const int nblk = (int)((N + median_block - 1) / median_block);
     const size_t post_sm = (size_t)median_block * (sizeof(float2) + sizeof(uint32_t));
-    fe_post<<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block);
+    if (!(n & (n - 1))) {
+        // power of two: the N-point FFT through the spectrum buffer into the workspace
+        const int p = log2i(N);
+        const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
+        const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
+        const int64_t N12 = (int64_t)N1 * N2;
+        fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(z, sp, N3, N12, N);
+        fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(sp, N1, N2);
+        fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(sp, wk, N1, N2,
+                                                                                 N3);
+        fe_post<false><<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block, 1.f);
+        return cuda_status(cudaGetLastError());
+    }
+    // Bluestein: workspace = [X | Bk | tmp], P complex each
+    const int64_t P = bluestein_length(n);
+    float2* X = wk;
+    float2* Bk = wk + P;
+    float2* tmp = wk + 2 * P;
+    const unsigned grid = (unsigned)std::min<int64_t>((P + kFeThreads - 1) / kFeThreads, 152 * 16);
+    bs_chirp_in<<<grid, kFeThreads, 0, st>>>(z, X, N, P);
+    bs_chirp_kernel<<<grid, kFeThreads, 0, st>>>(Bk, N, P);
+    if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
+    if ((rc = fft_pow2(X, tmp, X, P, st)) != FDAS_OK) return rc;
+    if ((rc = fft_pow2(Bk, tmp, Bk, P, st)) != FDAS_OK) return rc;
+    bs_mul_conj<<<grid, kFeThreads, 0, st>>>(X, Bk, P);
+    if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
+    if ((rc = fft_pow2(X, tmp, X, P, st)) != FDAS_OK) return rc;
+    fe_post<true><<<nblk, kFeThreads, post_sm, st>>>(X, sp, N, median_block, 1.0f / (float)P);
     return cuda_status(cudaGetLastError());
 }
 
@@ -361,7 +478,7 @@ static int noalloc_scratch(void** out) {
 
 extern "C" int fdas_normalise_noalloc(const float* series, int64_t n, int32_t median_block,
                                       float* spec, void* stream) {
-    if (n > FDAS_NOALLOC_MAX_N) return FDAS_E_UNSUPPORTED;
+    if (n > FDAS_NOALLOC_MAX_N || (n > 0 && (n & (n - 1)))) return FDAS_E_UNSUPPORTED;
     const size_t need = fdas_normalise_workspace_bytes(n);
     if (need == 0 || need > fdas::kNoallocScratchBytes) return FDAS_E_INVAL;
     void* work = nullptr;

@@ -8,6 +8,10 @@
 namespace fdas {
 
 constexpr int kMaxGroups = FDAS_MAX_GROUPS;
+// L = 1024 convolver: warps per CTA, each holding one of a unit's segments
+constexpr int kWarpSegments = 4;
+// ... and its CTAs per SM (registers allow 168 per thread)
+constexpr int kWarpCtasPerSm = 12 / kWarpSegments;
 
 // Template grid and bank-row bookkeeping derived from fdas_params.
 struct Grid {
@@ -35,7 +39,8 @@ inline int64_t positions(const fdas_params* p, int64_t nb) { return p->interbin 
 // Work items of one series of npos positions.  L = 2048, 4096 (one CTA per
 // segment FFT): (segment, template) pairs, for each group ceil(npos / (L - gM))
 // segments times gK templates.  L = 1024 (one warp per segment FFT): units of
-// one template on four consecutive segments, ceil(segments / 4) times gK.
+// one template on kWarpSegments consecutive segments, ceil(segments /
+// kWarpSegments) times gK.
 int64_t series_items(const Grid& g, int L, int64_t npos);
 
 // Complex values per template-bank row: L = 1024 rows hold 16 register pairs
@@ -60,8 +65,8 @@ int launch_correlate(const fdas_params* p, const Grid& g, const float2* spec, in
                      const fdas_fused_threshold* fused, int32_t* status, cudaStream_t st);
 int launch_correlate_batched(const fdas_params* p, const Grid& g, const fdas_trial* trials,
                              int32_t ntrials, int64_t total_items, const float4* bank,
-                             const fdas_fused_threshold* fused, int ctas_per_sm, int32_t* status,
-                             cudaStream_t st);
+                             const fdas_fused_threshold* fused, int ctas_per_sm, int tpb,
+                             int32_t* status, cudaStream_t st);
 struct ConvArgs;
 // The L = 1024 (one warp per segment FFT) convolver, wconv.cu: element type
 // `out` (0 float, FDAS_PLANE_F16, FDAS_PLANE_BF16), half-bin sampling when

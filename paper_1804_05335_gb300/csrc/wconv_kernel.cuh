@@ -1,9 +1,11 @@
 // The L = 1024 overlap-save convolver: one warp per segment FFT (Sections 3,
 // 4.1, 4.2).
 //
-// A CTA of NW = 4 warps takes a contiguous, statically balanced range of work
-// units in the order (series, template group, quad, template): a unit is one
-// template applied to the quad's four consecutive segments, one per warp.
+// A CTA of NW warps takes a contiguous, statically balanced range of work
+// units in the order (series, template group, template chunk, quad,
+// template): a unit is one template applied to the quad's NW consecutive
+// segments, one per warp (the chunk is the whole group unless a batched
+// launch asks for fewer templates per block).
 // When the quad changes, each warp loads its segment -- L bins starting at
 // s*B - M/2, zero outside the spectrum -- and runs the forward FFT once
 // (wfft.cuh), keeping the spectrum Y in registers.  Per unit, each warp
@@ -92,20 +94,29 @@ struct WSeries<true> {
     __device__ __forceinline__ int trial() const { return tr; }
 };
 
-// Walk over the work units of a series (or of a batch of series).
+// Walk over the work units of a series (or of a batch of series).  Within a
+// template group the units run (template chunk, quad, template): A.tpb > 0
+// splits the group's templates into chunks of A.tpb, each applied to every
+// quad before the next chunk (templates per CTA visit of a segment); A.tpb =
+// 0 keeps the whole group as one chunk, so each quad's forward FFT serves
+// all of the group's templates.
 template <bool BATCH, int SUB>
 struct WWalk {
     int64_t u;        // unit index
     WSeries<BATCH> ser;
     int nq;           // quads of group grp in the current series
-    int quad;         // segments 4 quad .. 4 quad + 3 of group grp
+    int quad;         // segments NW quad .. NW quad + NW - 1 of group grp
     int grp;
     int q;            // template of group grp
+    int c0, cn;       // current chunk: templates c0 .. c0 + cn - 1
 
     __device__ __forceinline__ int64_t npos(const ConvArgs& A) const { return SUB * ser.nb(A); }
     __device__ __forceinline__ int quads(const ConvArgs& A, int g) const {
         const int64_t B = WShape::L - A.gM[g];
         return (int)(((npos(A) + B - 1) / B + WShape::NW - 1) / WShape::NW);
+    }
+    __device__ __forceinline__ static int chunk(const ConvArgs& A, int g) {
+        return (A.tpb > 0 && A.tpb < A.gK[g]) ? A.tpb : A.gK[g];
     }
     __device__ __forceinline__ void init(const ConvArgs& A, int64_t u0) {
         u = u0;
@@ -127,20 +138,30 @@ struct WWalk {
             ++grp;
             nq = quads(A, grp);
         }
-        quad = (int)(rel / A.gK[grp]);
-        q = (int)(rel - (int64_t)quad * A.gK[grp]);
+        const int C = chunk(A, grp);
+        c0 = (int)min(rel / ((int64_t)nq * C), (int64_t)((A.gK[grp] - 1) / C)) * C;
+        cn = min(C, A.gK[grp] - c0);
+        rel -= (int64_t)nq * c0;
+        quad = (int)(rel / cn);
+        q = c0 + (int)(rel - (int64_t)quad * cn);
     }
     // next unit; returns true if it starts a new quad (new segments)
     __device__ __forceinline__ bool advance(const ConvArgs& A) {
         ++u;
         bool fresh = false;
-        if (++q == A.gK[grp]) {
-            q = 0;
+        if (++q == c0 + cn) {
+            q = c0;
             fresh = true;
             if (++quad == nq) {
                 quad = 0;
-                if (++grp == A.ng) grp = 0;
-                nq = quads(A, grp);
+                c0 += cn;
+                if (c0 == A.gK[grp]) {
+                    c0 = 0;
+                    if (++grp == A.ng) grp = 0;
+                    nq = quads(A, grp);
+                }
+                cn = min(chunk(A, grp), A.gK[grp] - c0);
+                q = c0;
             }
         }
         if constexpr (BATCH) {
@@ -148,6 +169,8 @@ struct WWalk {
                 ser.set(A, ser.trial() + 1);
                 grp = 0;
                 quad = 0;
+                c0 = 0;
+                cn = chunk(A, 0);
                 q = 0;
                 nq = quads(A, 0);
                 fresh = true;
@@ -336,11 +359,10 @@ __device__ __forceinline__ float wepi_staged(const float2* v, float2* xb, int l,
 // Forward FFT of one segment (a warp's, once per quad): positions base + l +
 // 32 i of the series (zero outside it; SUB = 2: the spectrum with zeros
 // interleaved, npos = 2 nb), transformed by wfft_forward and left in the
-// warp's buffer as xb[i*32 + l] = X[l + 32 i].  Not inlined: it runs once
-// per quad, and keeping its code out of the per-template loop keeps that
-// loop small in the instruction cache.
+// warp's buffer as xb[i*32 + l] = X[l + 32 i].  (Measured: as a called
+// function it was 3 % slower than inlined.)
 template <int SUB>
-__device__ __noinline__ void wseg_forward(const float2* __restrict__ spec, int64_t nb, int64_t base,
+__device__ __forceinline__ void wseg_forward(const float2* __restrict__ spec, int64_t nb, int64_t base,
                                           float2* xb, const float4* tw4, int l) {
     float2 v[32];
 #pragma unroll
@@ -360,7 +382,7 @@ __device__ __noinline__ void wseg_forward(const float2* __restrict__ spec, int64
 }
 
 template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB>
-__global__ void __launch_bounds__(WShape::NW * 32, 3) wconv_kernel(const ConvArgs A) {
+__global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(const ConvArgs A) {
     constexpr int NW = WShape::NW, NBUF = WShape::NBUF, ROW4 = WShape::ROW4, L = WShape::L;
     extern __shared__ float4 wsm4[];
     float4* hbuf = wsm4;                                   // NBUF rows of ROW4

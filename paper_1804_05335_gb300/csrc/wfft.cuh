@@ -17,13 +17,14 @@
 // __syncwarp, never a CTA barrier.
 #pragma once
 #include "dft.cuh"
+#include "internal.h"
 
 namespace fdas {
 
 struct WShape {
     static constexpr int L = 1024;
-    static constexpr int NW = 4;            // warps (one segment each) per convolver CTA
-    static constexpr int NBUF = 3;          // bank rows staged per convolver CTA
+    static constexpr int NW = kWarpSegments;   // warps (one segment each) per convolver CTA
+    static constexpr int NBUF = 2;          // bank rows staged per convolver CTA (measured: 2 beats 3)
     // bank row: 16 register pairs x (32 lanes + a mirror column), float4 each
     static constexpr int ROW4 = 16 * 33;
     static constexpr int XS = 34;           // exchange row stride in float2 (32 + 2 pad)

@@ -42,6 +42,13 @@ def test_host_helpers():
     assert [F.fdas_half_width(z) for z in (0, 1, -21, 200)] == [8, 9, 19, 108]
     assert F.fdas_normalise_workspace_bytes(1 << 23) == (1 << 22) * 8
     assert F.fdas_normalise_workspace_bytes(1000) == 0
+    # even lengths that are not powers of two: three buffers of the power-of-two
+    # convolution length P >= n - 1
+    assert F.fdas_normalise_workspace_bytes(100000) == 3 * (1 << 17) * 8
+    assert F.fdas_normalise_workspace_bytes(8194) == 3 * (1 << 14) * 8
+    assert F.fdas_normalise_workspace_bytes((1 << 24) - 2) == 3 * (1 << 24) * 8
+    assert F.fdas_normalise_workspace_bytes(100001) == 0          # odd
+    assert F.fdas_normalise_workspace_bytes((1 << 24) + 2) == 0   # past the largest convolution
     assert F.fdas_strerror(F.FDAS_E_INVAL) == "invalid argument"
 
 
@@ -73,7 +80,9 @@ def test_invalid_buffers_rejected_before_launch():
         lambda: F.fdas_correlate(p, 256, 0, 256, 256, 2000, stream=0),        # nb < 1
         lambda: F.fdas_make_templates(p, 0, stream=0),
         lambda: F.fdas_make_templates(p, 8, stream=0),
-        lambda: F.fdas_normalise(256, 1000, 1024, 256, 256, 1 << 20, stream=0),    # n not 2^k
+        lambda: F.fdas_normalise(256, 1000, 1024, 256, 256, 1 << 20, stream=0),    # n too small
+        lambda: F.fdas_normalise(256, 100001, 1024, 256, 256, 1 << 24, stream=0),  # n odd
+        lambda: F.fdas_normalise(256, 100000, 1024, 256, 256, 1 << 20, stream=0),  # work size
         lambda: F.fdas_normalise(256, 1 << 14, 16, 256, 256, 1 << 20, stream=0),   # block
         lambda: F.fdas_normalise(256, 1 << 14, 1024, 256, 256, 100, stream=0),     # work size
         lambda: F.fdas_threshold(256, 0, 10, 10, 20.0, 0, 256, 4, 256, stream=0),  # rows

@@ -92,26 +92,52 @@ def test_batched_graph_replay(F):
 def test_autotune_picks_a_candidate(F, tmp_path):
     from paper_1804_05335_gb300.autotune import autotune
     path = str(tmp_path / "tune.json")
-    res = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=((1024, 0), (2048, 0), (2048, 1)),
-                   cache_path=path)
-    assert (res["L"], res["ctas_per_sm"]) in ((1024, 0), (2048, 0), (2048, 1))
-    assert len(res["ms"]) == 3 and all(v > 0 for v in res["ms"].values())
-    again = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=((1024, 0), (2048, 0), (2048, 1)),
-                     cache_path=path)
+    cands = ((1024, 0, 0), (1024, 0, 5), (2048, 0, 0), (2048, 1, 0))
+    res = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=cands, cache_path=path)
+    assert (res["L"], res["ctas_per_sm"], res["templates_per_block"]) in cands
+    assert len(res["ms"]) == 4 and all(v > 0 for v in res["ms"].values())
+    again = autotune([1 << 15, 1 << 14], 64, -20, 20, 2, candidates=cands, cache_path=path)
     assert again == res
+
+
+@pytest.mark.parametrize("tpb", [1, 7, 26, 500])
+def test_templates_per_block_keeps_every_plane(F, tpb):
+    """Chunking a group's templates (templates per block) only reorders the
+    work: planes and candidates equal the default order's, bit for bit, on the
+    production bank with uneven lengths that are not powers of two."""
+    from paper_1804_05335_gb300.batch import BatchSearch
+    ns = [20002, 65536, 9000, 131074]
+    ref = None
+    for t in (0, tpb):
+        bs = BatchSearch(ns, 1024, 256, -200, 200, 2, thr=20.0, ctas_per_sm=1,
+                         templates_per_block=t)
+        for i, n in enumerate(ns):
+            bs.set_series(i, synth.make_series(n, ((n / 4 + 0.2, 90.0, 18.0),), 600 + i))
+        bs.run()
+        torch.cuda.synchronize()
+        planes = [bs.plane_of(i).cpu().numpy().copy() for i in range(len(ns))]
+        cands, counts = bs.candidates()
+        if ref is None:
+            ref = (planes, cands)
+            continue
+        for i in range(len(ns)):
+            assert np.array_equal(planes[i], ref[0][i]), (tpb, i)
+            for a, b in zip(cands[i], ref[1][i]):
+                assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("L", [1024, 2048])
 def test_batched_production_bank(F, L):
     """The production template bank (z = -200..200 step 2, M = 256: four
-    template groups of increasing overlap) in the batched launch, with one CTA
-    per SM so that each CTA's range crosses trial and group boundaries, and a
-    pool small enough for several waves: every trial's spectrum, plane and
-    candidate list are bit-identical to the single-series call, and a trial
-    that is not the first of its wave matches the FP64 oracle."""
+    template groups of increasing overlap) in the batched launch, on trials of
+    uneven length (most of them not powers of two), with one CTA per SM so
+    that each CTA's range crosses trial and group boundaries, and a pool small
+    enough for several waves: every trial's spectrum, plane and candidate list
+    are bit-identical to the single-series call, and a trial that is not the
+    first of its wave matches the FP64 oracle."""
     from paper_1804_05335_gb300.batch import BatchSearch
     from paper_1804_05335_gb300.search import Search
-    ns = [1 << 13, 1 << 15, 1 << 14, 1 << 16, 1 << 13, 1 << 14]
+    ns = [8194, 40000, 1 << 14, 70002, 12288, 1 << 15]
     bs = BatchSearch(ns, L, 256, -200, 200, 2, thr=20.0, pool_bytes=64 << 20, ctas_per_sm=1)
     assert len(bs.waves) > 1
     assert len(F.fdas_template_groups(bs.p)) == 4
