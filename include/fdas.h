@@ -180,7 +180,9 @@ int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
  */
 int fdas_make_templates(const fdas_params *p, float *bank, void *stream);
 
-/* Workspace bytes fdas_normalise needs for n samples (0 if n unsupported). */
+/* Workspace bytes fdas_normalise needs for n samples (0 if n unsupported):
+ * n/2 complex values for a power of two, 3 P (P the least power of two
+ * >= n - 1) for the other even lengths. */
 size_t fdas_normalise_workspace_bytes(int64_t n);
 
 /*
@@ -192,8 +194,12 @@ size_t fdas_normalise_workspace_bytes(int64_t n);
  *   consecutive bins (the last block takes the remainder), m = the lower
  *   median (rank floor((len-1)/2)) of |X_k|^2 in the block, and
  *   spec_k = X_k / sqrt(m / ln 2)  (0 if m == 0), so noise power has mean 1.
- * series: (device) n floats, 8-byte aligned.  n: power of two,
- *   2^13 <= n <= 2^25.  median_block: 32..8192.
+ * series: (device) n floats, 8-byte aligned.  n: a power of two with
+ *   2^13 <= n <= 2^25, or any even n with 2^13 < n <= 2^24; the N = n/2
+ *   point DFT of the packed samples then runs as Bluestein's chirp-z
+ *   convolution, Z_k = c_k sum_m (z_m c_m) conj(c_{k-m}), c_m = exp(-i pi
+ *   m^2/N), with power-of-two FFTs of length P >= n - 1.  median_block:
+ *   32..8192.
  * spec: (device) n/2 complex, written.
  * work: (device) fdas_normalise_workspace_bytes(n) bytes, 16-byte aligned;
  *   scratch, contents undefined afterwards.
@@ -224,7 +230,8 @@ int fdas_normalise(const float *series, int64_t n, int32_t median_block, float *
  * must not be issued.  The array needs no clearing between calls (every
  * value is written before it is read).
  * Arguments, layout and results are those of fdas_normalise.
- * Errors: FDAS_E_UNSUPPORTED if n > FDAS_NOALLOC_MAX_N; otherwise as
+ * Errors: FDAS_E_UNSUPPORTED if n > FDAS_NOALLOC_MAX_N or n is not a power
+ * of two (other lengths need a larger workspace); otherwise as
  * fdas_normalise; FDAS_E_CUDA if the array's address cannot be obtained.
  */
 int fdas_normalise_noalloc(const float *series, int64_t n, int32_t median_block, float *spec,

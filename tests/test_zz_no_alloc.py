@@ -15,16 +15,17 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# the tolerance the normalise parity tests use against the oracle
-TOL = 2e-4
-
 
 def test_noalloc_normalise_matches_workspace_version_twice():
+    """The same kernels on the same input with another workspace address:
+    the spectra must be bit-identical, call after call.  Large, small, then
+    large again: a stale value left in the shared array by the larger call
+    would show in the smaller one, and the reverse."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1804_05335_gb300 as F
     F.load_library()
-    cases = [(F.FDAS_NOALLOC_MAX_N, 1024, 11), (1 << 15, 512, 12)]   # two calls in a row
+    cases = [(F.FDAS_NOALLOC_MAX_N, 1024, 11), (1 << 15, 512, 12), (F.FDAS_NOALLOC_MAX_N, 1024, 13)]
     for n, block, seed in cases:
         x = synth.make_series(n, ((n / 9 + 0.4, 8.0, 18.0),), seed)
         series = torch.from_numpy(x).cuda()
@@ -35,12 +36,11 @@ def test_noalloc_normalise_matches_workspace_version_twice():
         F.fdas_normalise(series, n, block, ref, work, ws)
         F.fdas_normalise_noalloc(series, n, block, got)
         torch.cuda.synchronize()
-        diff = (got - ref).abs().max().item()
-        assert diff <= TOL, (n, diff)
+        assert torch.equal(got, ref), (n, (got - ref).abs().max().item())
         assert got[0].item() == 0
 
 
-def test_noalloc_rejects_sizes_above_its_limit():
+def test_noalloc_rejects_sizes_above_its_limit_and_other_lengths():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1804_05335_gb300 as F
@@ -49,4 +49,8 @@ def test_noalloc_rejects_sizes_above_its_limit():
     spec = torch.zeros(n // 2, dtype=torch.complex64, device="cuda")
     with pytest.raises(F.FdasError) as e:
         F.fdas_normalise_noalloc(series, n, 1024, spec)
+    assert e.value.code == F.FDAS_E_UNSUPPORTED
+    # lengths that are not powers of two need Bluestein's larger workspace
+    with pytest.raises(F.FdasError) as e:
+        F.fdas_normalise_noalloc(series, 100000, 1024, spec)
     assert e.value.code == F.FDAS_E_UNSUPPORTED
