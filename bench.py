@@ -590,54 +590,65 @@ def significance_row(args, torch, dev, S, wl):
 
 
 def split_row(args, torch, dev, S, wl):
-    """The production plane with the four radix-16 DFT passes of every segment
-    FFT on tensor cores (FP16 hi+lo, BF16 hi+lo and BF16 hi+mid+lo operands,
-    FP32 accumulation): convolver time, and plane and candidate-list
-    differences against the FP32 form on the same spectrum (errors against the
-    FP64 oracle come from tests/test_gpu_split.py::test_split_production_error_table).
-    The split forms exist for L = 2048 and 4096; a step at L = 1024 is
-    measured here on its spectrum at L = 2048."""
-    if S.L == 1024:
-        from paper_1804_05335_gb300.search import Search
-        S2 = Search(wl.n, 2048, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
-                    median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
-        S2.spec.copy_(S.spec)
-        S2.make_templates()
-        S = S2
-    S.correlate(fused=True)
-    rf, cf, pf, _, _ = S.candidates()
-    fp32 = {(int(r), int(c)) for r, c in zip(rf, cf)}
-    ref = S.plane.clone()
-    out = {}
+    """The production plane with the DFT passes of every segment FFT on tensor
+    cores: at L = 1024 the radix-32 passes of the warp convolver with tcgen05
+    (operands in tensor and shared memory, FP32 accumulators in tensor
+    memory), at L = 2048 the radix-16 passes of the CTA convolver with
+    warp-level mma.sync; FP16 hi+lo, BF16 hi+lo and BF16 hi+mid+lo operands.
+    Convolver time, and plane and candidate-list differences against the FP32
+    form on the same spectrum (errors against the FP64 oracle come from
+    tests/test_gpu_split.py::test_split_production_error_table)."""
+    from paper_1804_05335_gb300.search import Search
+    res = {}
     reps = 10
-    for name, prec in (("fp32", 0), ("fp16_split", 1), ("bf16_split", 2), ("bf16x3_split", 3)):
-        for _ in range(3):
-            S.correlate(fused=True, prec=prec)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            S.correlate(fused=True, prec=prec)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        r, c, p, _, tot = S.candidates()
-        got = {(int(a), int(b)) for a, b in zip(r, c)}
-        a2 = S.plane.view(S.K, S.row_stride)
-        b2 = ref.view(S.K, S.row_stride)
-        dmax, dsq = 0.0, 0.0
-        for k0 in range(0, S.K, 16):
-            d = (a2[k0:k0 + 16, : S.width] - b2[k0:k0 + 16, : S.width]).abs()
-            dmax = max(dmax, float(d.max()))
-            dsq += float(d.double().square().sum())
-        out[name] = {"conv_ms": ms, "points_per_s": S.K * S.width / (ms / 1e3),
-                     "vs_fp32_plane": {"max_abs": dmax, "rms": (dsq / (S.K * S.width)) ** 0.5},
-                     "candidates": int(tot), "only_here": len(got - fp32),
-                     "only_in_fp32": len(fp32 - got)}
-    del ref
-    return {"workload": "production plane, L=%d" % S.L, "reps": reps, "forms": out,
-            "dft_passes_on_tensor_cores": "radix-16 passes of forward and inverse FFTs "
-                                          "(mma.sync m16n8k16; 3 products per pass, 6 for "
-                                          "bf16x3)"}
+    for L in (1024, 2048):
+        if S.L == L:
+            T = S
+        else:
+            T = Search(wl.n, L, wl.M, wl.zmin, wl.zmax, wl.zstep, interbin=1,
+                       median_block=wl.median_block, thr=wl.threshold, cap=args.cap, device=dev)
+            T.spec.copy_(S.spec)
+            T.make_templates()
+        T.correlate(fused=True)
+        rf, cf, pf, _, _ = T.candidates()
+        fp32 = {(int(r), int(c)) for r, c in zip(rf, cf)}
+        ref = T.plane.clone()
+        out = {}
+        for name, prec in (("fp32", 0), ("fp16_split", 1), ("bf16_split", 2), ("bf16x3_split", 3)):
+            for _ in range(3):
+                T.correlate(fused=True, prec=prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                T.correlate(fused=True, prec=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            r, c, p, _, tot = T.candidates()
+            got = {(int(a), int(b)) for a, b in zip(r, c)}
+            a2 = T.plane.view(T.K, T.row_stride)
+            b2 = ref.view(T.K, T.row_stride)
+            dmax, dsq = 0.0, 0.0
+            for k0 in range(0, T.K, 16):
+                d = (a2[k0:k0 + 16, : T.width] - b2[k0:k0 + 16, : T.width]).abs()
+                dmax = max(dmax, float(d.max()))
+                dsq += float(d.double().square().sum())
+            out[name] = {"conv_ms": ms, "points_per_s": T.K * T.width / (ms / 1e3),
+                         "vs_fp32_plane": {"max_abs": dmax, "rms": (dsq / (T.K * T.width)) ** 0.5},
+                         "candidates": int(tot), "only_here": len(got - fp32),
+                         "only_in_fp32": len(fp32 - got)}
+        del ref
+        if T is not S:
+            del T
+            torch.cuda.empty_cache()
+        res["L%d" % L] = {
+            "forms": out,
+            "dft_passes_on_tensor_cores":
+                ("radix-32 passes of the forward and inverse FFTs as tcgen05.mma "
+                 "(M=128 instances, N=K=64; 3 products, 6 for bf16x3)") if L == 1024 else
+                ("radix-16 passes of the forward and inverse FFTs as mma.sync m16n8k16 "
+                 "(3 products, 6 for bf16x3)")}
+    return {"workload": "production plane", "reps": reps, "segments": res}
 
 
 def refine_row(args, torch, dev, S, wl):

@@ -287,7 +287,7 @@ int fdas_correlate_split(const fdas_params* p, int32_t prec, const float* spec, 
     Grid g;
     int rc = check_correlate(p, &g, spec, nb, bank, plane, row_stride, fused, status);
     if (rc != FDAS_OK) return rc;
-    if (prec != FDAS_PREC_FP32 && (p->interbin == 2 || p->L == 1024)) return FDAS_E_UNSUPPORTED;
+    if (prec != FDAS_PREC_FP32 && p->interbin == 2) return FDAS_E_UNSUPPORTED;
     if (prec == FDAS_PREC_FP32)
         return launch_correlate(p, g, reinterpret_cast<const float2*>(spec), nb,
                                 reinterpret_cast<const float4*>(bank), plane, row_stride, fused,

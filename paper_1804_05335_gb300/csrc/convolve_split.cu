@@ -1,6 +1,8 @@
 // fdas_correlate_split: the convolver with its radix-16 DFT passes as
-// split-precision tensor-core products (kernel in conv_kernel.cuh, DFT in
-// split_mma.cuh).  Single-series launches, L = 2048 and 4096.
+// split-precision tensor-core products: warp-level mma.sync in the CTA
+// convolver for L = 2048 and 4096 (conv_kernel.cuh, split_mma.cuh), tcgen05
+// with tensor memory in the warp convolver for L = 1024 (wconv_split.cu,
+// tc_dft.cuh).  Single-series launches.
 #include "conv_kernel.cuh"
 
 namespace fdas {
@@ -8,6 +10,8 @@ namespace fdas {
 template <int PREC>
 static int dispatch_split(const fdas_params* p, const ConvArgs& a, bool fused, cudaStream_t st) {
     switch (p->L) {
+        case 1024:
+            return dispatch_wconv_split(p, a, fused, PREC, st);
         case 2048:
             return fused ? launch_one<2048, true, false, PREC>(a, 0, st)
                          : launch_one<2048, false, false, PREC>(a, 0, st);

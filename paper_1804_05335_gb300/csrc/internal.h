@@ -73,6 +73,10 @@ struct ConvArgs;
 // p->interbin == 2.
 int dispatch_wconv(const fdas_params* p, const ConvArgs& a, bool fused, bool batch, int out,
                    int ctas_per_sm, cudaStream_t st);
+// The L = 1024 convolver with its DFT passes on the tensor cores
+// (fdas_correlate_split, wconv_split.cu).
+int dispatch_wconv_split(const fdas_params* p, const ConvArgs& a, bool fused, int prec,
+                         cudaStream_t st);
 // The L = 1024 convolver with its first template row's barrier armed and
 // no copy issued, `polls` polls per wait (fdas_debug_wait_timeout).
 int launch_wconv_wait_probe(const fdas_params* p, const Grid& g, const float2* spec, int64_t nb,

@@ -38,16 +38,20 @@
 // waits, again bounded, for its copies still in flight before the CTA exits.
 #pragma once
 #include "conv_common.cuh"
+#include "tc_dft.cuh"
 #include "tma.cuh"
 #include "wfft.cuh"
 
 namespace fdas {
 
+template <int PREC = 0>
 struct WSmem {
-    static constexpr size_t bytes =
+    static constexpr size_t base =
         (size_t)WShape::NBUF * WShape::ROW4 * sizeof(float4) +     // staged bank rows
         (size_t)WShape::TW4 * sizeof(float4) +                       // twiddle table
         (size_t)WShape::NW * WShape::XBUF * sizeof(float2);          // per-warp exchange
+    // tensor-core forms: the DFT matrix parts (tc_dft.cuh)
+    static constexpr size_t bytes = base + (PREC ? (size_t)TcShape<PREC ? PREC : 1>::BBYTES : 0);
 };
 
 template <int I>
@@ -381,8 +385,13 @@ __device__ __forceinline__ void wseg_forward(const float2* __restrict__ spec, in
     __syncwarp();
 }
 
-template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB>
-__global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(const ConvArgs A) {
+// PREC 0: the 32-point DFT passes in FP32 on the CUDA cores; PREC 1, 2, 3:
+// on the tensor cores (tc_dft.cuh), FP16 hi+lo, BF16 hi+lo, BF16 hi+mid+lo.
+// The tensor-core forms hold two CTAs per SM (their DFT matrix parts take
+// shared memory, and two CTAs' tensor memory fits the SM's 512 columns).
+template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB, int PREC = 0>
+__global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
+    wconv_kernel(const ConvArgs A) {
     constexpr int NW = WShape::NW, NBUF = WShape::NBUF, ROW4 = WShape::ROW4, L = WShape::L;
     extern __shared__ float4 wsm4[];
     float4* hbuf = wsm4;                                   // NBUF rows of ROW4
@@ -391,6 +400,8 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
     __shared__ uint64_t full[NBUF], empty[NBUF];
     __shared__ volatile int abort_flag;
     __shared__ WProducer<BATCH, SUB> prod;
+    __shared__ uint64_t tc_ready, tc_done;
+    __shared__ uint32_t tc_tmem;
 
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     float2* xb = xall + w * WShape::XBUF;
@@ -434,17 +445,69 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
     };
 
     wfft_twiddles(tw4, tid, NW * 32);
+    constexpr int TP = PREC ? PREC : 1;
+    unsigned char* wparts = reinterpret_cast<unsigned char*>(xall + NW * WShape::XBUF);
+    if constexpr (PREC != 0) {
+        tc_fill_w<TP>(wparts, tid, NW * 32);
+        fence_proxy_async();   // the DFT matrix is read by the tensor cores
+        if (w == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(&tc_tmem)), "r"((uint32_t)TcShape<TP>::NCOLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+    }
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], NW);
+        }
+        if constexpr (PREC != 0) {
+            mbar_init(&tc_ready, NW);
+            mbar_init(&tc_done, 1);
         }
         abort_flag = 0;
         prod.walk = cw;
         prod.issued = 0;
         produce(NBUF - 1);
     }
+    if constexpr (PREC != 0) tc_fence_before();
     __syncthreads();
+    TcCtx tc;
+    if constexpr (PREC != 0) {
+        tc_fence_after();
+        tc.tmem = tc_tmem;
+        tc.wsm = smem_u32(wparts);
+        tc.ready = &tc_ready;
+        tc.done = &tc_done;
+        tc.phase = 0;
+        tc.commits = 0;
+    }
+    // one 32-point DFT pass of the inverse (PREC 0: in registers)
+    auto pass = [&](float2* x) -> bool {
+        if constexpr (PREC == 0) {
+            dft32<1>(x);
+            return true;
+        } else {
+            return tc_dft32<TP>(x, tc, tid, &abort_flag, limit);
+        }
+    };
+    // the inverse transform, k = l + 32 i -> p = l + 32 i (wfft_inverse's steps)
+    auto inverse = [&](float2* x) -> bool {
+#pragma unroll 1
+        for (int ps = 0; ps < 2; ++ps) {
+            if (!pass(x)) return false;
+            if (ps == 0) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float4 t = tw4[j * 32 + l];
+                    if (j) x[2 * j] = cmul(x[2 * j], make_float2(t.x, t.y));
+                    x[2 * j + 1] = cmul(x[2 * j + 1], make_float2(t.z, t.w));
+                }
+                wfft_transpose(x, xb, l);
+            }
+        }
+        return true;
+    };
 
     float2 Y[32], v[32];
     bool fresh = true, live = false, fast = false;
@@ -464,11 +527,33 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
             fast = M2 <= 160 && r0 + B <= npos;
             ilo = (M2 - l + 31) >> 5;               // first register at position >= M/2
             ihi = (L - M2 - l + 31) >> 5;           // first register at position >= M/2 + B
-            if (live) {
-                wseg_forward<SUB>(cw.ser.spec(A), cw.ser.nb(A), r0 - M2, xb, tw4, l);
+            if constexpr (PREC == 0) {
+                if (live) {
+                    wseg_forward<SUB>(cw.ser.spec(A), cw.ser.nb(A), r0 - M2, xb, tw4, l);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) Y[i] = xb[i * 32 + l];
-                __syncwarp();
+                    for (int i = 0; i < 32; ++i) Y[i] = xb[i * 32 + l];
+                    __syncwarp();
+                }
+            } else {
+                // every warp takes part in the CTA's tensor-core passes (a segment
+                // past the series transforms zeros); forward = conj(inverse(conj))
+                const float2* sp = cw.ser.spec(A);
+                const int64_t base = r0 - M2 + l, nbs = cw.ser.nb(A);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int64_t pos = base + 32 * i;
+                    float2 z;
+                    if constexpr (SUB == 1) {
+                        z = (pos >= 0 && pos < nbs) ? __ldg(&sp[pos]) : make_float2(0.f, 0.f);
+                    } else {
+                        z = (pos >= 0 && pos < 2 * nbs && !(pos & 1)) ? __ldg(&sp[pos >> 1])
+                                                                      : make_float2(0.f, 0.f);
+                    }
+                    Y[i] = make_float2(z.x, -z.y);
+                }
+                if (!inverse(Y)) break;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) Y[i].y = -Y[i].y;
             }
         }
         if (brow != cur_brow) {
@@ -490,7 +575,7 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
                 break;
             }
         }
-        if (live) {
+        if (live || PREC != 0) {
             // ---- multiply by the template spectrum ----
             const float4* hr = hbuf + (ri % NBUF) * ROW4;
             if (!cj) {
@@ -509,7 +594,15 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
                 }
             }
             // ---- inverse FFT ----
-            wfft_inverse(v, xb, tw4, l);
+            if constexpr (PREC == 0) {
+                wfft_inverse(v, xb, tw4, l);
+            } else {
+                if (!inverse(v)) break;
+                if (!live) {
+                    fresh = cw.advance(A);
+                    continue;
+                }
+            }
             // ---- powers of positions M/2 .. M/2 + B - 1 ----
             void* prow = OUT == 0 ? static_cast<void*>(cw.ser.plane(A) + (int64_t)row * cw.ser.row_stride(A))
                                   : static_cast<void*>(reinterpret_cast<uint16_t*>(cw.ser.plane(A)) +
@@ -537,20 +630,38 @@ __global__ void __launch_bounds__(WShape::NW * 32, kWarpCtasPerSm) wconv_kernel(
             const int never = 0;
             wwait(&full[k % NBUF], (k / NBUF) & 1, &never, limit);
         }
+        if constexpr (PREC != 0) {
+            // nor may tensor-core products still be running on its tensor memory
+            if (tc.commits > 0) mbar_wait_bounded(&tc_done, (tc.commits - 1) & 1u, limit);
+        }
+    }
+    if constexpr (PREC != 0) {
+        // every wait above is bounded, so every thread arrives here
+        tc_fence_before();
+        __syncthreads();
+        if (w == 0) {
+            tc_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                         ::"r"(tc.tmem), "r"((uint32_t)TcShape<TP>::NCOLS) : "memory");
+        }
     }
 }
 
-template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB>
+template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB, int PREC = 0>
 static int launch_w(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
-    constexpr size_t smem = WSmem::bytes;
+    constexpr size_t smem = WSmem<PREC>::bytes;
     int sms = 0, max_per_sm = 0;
     const int rc = kernel_setup(
-        reinterpret_cast<const void*>(&wconv_kernel<FUSE, BATCH, OUT, SUB, IB>), smem,
+        reinterpret_cast<const void*>(&wconv_kernel<FUSE, BATCH, OUT, SUB, IB, PREC>), smem,
         WShape::NW * 32, &sms, &max_per_sm);
     if (rc != FDAS_OK) return rc;
-    const int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
+    int per = (ctas_per_sm > 0 && ctas_per_sm < max_per_sm) ? ctas_per_sm : max_per_sm;
+    // tensor memory: the CTAs resident on an SM must fit its 512 columns, or
+    // an allocation would wait for another CTA to finish
+    if (PREC != 0) per = std::min(per, 512 / TcShape<PREC ? PREC : 1>::NCOLS);
+    if (PREC != 0 && max_per_sm > 512 / TcShape<PREC ? PREC : 1>::NCOLS) return FDAS_E_UNSUPPORTED;
     const int64_t g = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(1, args.items));
-    wconv_kernel<FUSE, BATCH, OUT, SUB, IB><<<(unsigned)g, WShape::NW * 32, smem, st>>>(args);
+    wconv_kernel<FUSE, BATCH, OUT, SUB, IB, PREC><<<(unsigned)g, WShape::NW * 32, smem, st>>>(args);
     return cuda_status(cudaGetLastError());
 }
 

@@ -1,6 +1,7 @@
-"""GPU parity of fdas_correlate_split, the convolver whose radix-16 DFT passes
-run as split-precision tensor-core products, against the FP64 oracle and
-against the FP32 form on the same spectrum.
+"""GPU parity of fdas_correlate_split, the convolver whose DFT passes run as
+split-precision tensor-core products (radix 32 with tcgen05 and tensor memory
+at L = 1024, radix 16 with mma.sync at L = 2048 and 4096), against the FP64
+oracle and against the FP32 form on the same spectrum.
 
 Tolerances on normalised power (noise mean 1), |P_gpu - P_ref| <= a + b P_ref:
   FP32 through this entry: bit-identical to fdas_correlate.
@@ -54,6 +55,9 @@ def _within(got, ref, prec):
 
 CASES = [
     # n, L, M, zmin, zmax, zstep, interbin
+    (1 << 14, 1024, 64, -20, 20, 2, 1),      # tcgen05 radix-32 passes, ragged tail
+    (1 << 14, 1024, 128, -10, 30, 5, 1),     # tcgen05, asymmetric grid
+    (1 << 14, 1024, 64, -20, 20, 2, 0),      # tcgen05, no interbinning
     (1 << 14, 2048, 64, -20, 20, 2, 1),      # ragged tail
     (1 << 14, 4096, 128, -20, 20, 2, 1),
     (1 << 14, 2048, 64, -21, 21, 2, 1),      # symmetric grid without z = 0
@@ -79,16 +83,6 @@ def test_split_plane_matches_oracle(F, prec, n, L, M, zmin, zmax, zstep, ib):
     assert ok, (NAMES[prec], emax)
 
 
-def test_split_rejects_warp_segment_length(F):
-    """L = 1024 runs the one-warp-per-segment convolver, which has no split form."""
-    S = _search(n=1 << 14, L=1024, M=64, zmin=-20, zmax=20, zstep=2)
-    S.make_templates()
-    for prec in (1, 2, 3):
-        with pytest.raises(F.FdasError) as e:
-            S.correlate(fused=False, prec=prec)
-        assert e.value.code == F.FDAS_E_UNSUPPORTED
-
-
 def test_split_fp32_entry_is_fdas_correlate(F):
     n = 1 << 14
     x = synth.make_series(n, ((2000.5, 8.0, 15.0),), 11)
@@ -104,10 +98,11 @@ def test_split_fp32_entry_is_fdas_correlate(F):
 
 
 @PRECS
-def test_split_tiny_and_odd_spectra(F, prec):
+@pytest.mark.parametrize("L", [1024, 2048])
+def test_split_tiny_and_odd_spectra(F, prec, L):
     for nb in (1, 5, 999, 1793):
         A = synth.random_spectrum(nb, 40 + nb)
-        S = _search(n=1 << 12, L=2048, M=256, zmin=-40, zmax=40, zstep=4)
+        S = _search(n=1 << 12, L=L, M=256, zmin=-40, zmax=40, zstep=4)
         S.spec[:nb].copy_(torch.from_numpy(A))
         S.make_templates()
         S.plane.fill_(-7.0)
@@ -119,7 +114,8 @@ def test_split_tiny_and_odd_spectra(F, prec):
         assert np.all(P[:, 2 * nb:] == -7.0)
 
 
-def test_fp16_split_keeps_range_on_strong_lines(F):
+@pytest.mark.parametrize("L", [1024, 2048])
+def test_fp16_split_keeps_range_on_strong_lines(F, L):
     """Lines of amplitude 1e5 and 7e4 (above FP16's largest finite value 65504)
     stay finite and accurate: the per-instance scaling keeps every operand
     inside FP16's exponent range."""
@@ -128,7 +124,7 @@ def test_fp16_split_keeps_range_on_strong_lines(F):
     A[1500] += 1.0e5
     A[4200] -= 7.0e4j
     A = A.astype(np.complex64)
-    S = _search(n=2 * nb, L=2048, M=64, zmin=-20, zmax=20, zstep=2)
+    S = _search(n=2 * nb, L=L, M=64, zmin=-20, zmax=20, zstep=2)
     S.spec[:nb].copy_(torch.from_numpy(A))
     S.make_templates()
     S.correlate(fused=False, nb=nb, prec=1)
@@ -149,7 +145,8 @@ def _production_windows(wl):
 
 
 def test_split_production_error_table(F):
-    """2^23-sample series, zmax = 200, at L = 2048 and 4096: every form's
+    """2^23-sample series, zmax = 200, at L = 1024 (tcgen05 radix-32 passes),
+    2048 and 4096 (mma.sync radix-16 passes): every form's
     power error against the FP64 oracle on 18 windows of 256 bins (8 random,
     both ends, every injection) over all 201 rows, and its fused candidate
     list against the FP32 form's.  FP32, FP16 hi+lo and BF16 hi+mid+lo must
@@ -163,7 +160,7 @@ def test_split_production_error_table(F):
     starts = _production_windows(wl)
     refs = {r0: O.plane_window(A64, zs, r0, 256) for r0 in starts}
     table = {}
-    for L in (2048, 4096):
+    for L in (1024, 2048, 4096):
         S = _search(n=wl.n, L=L, M=wl.M, zmin=wl.zmin, zmax=wl.zmax, zstep=wl.zstep,
                     thr=wl.threshold, cap=1 << 16)
         S.spec.copy_(torch.from_numpy(A))
@@ -205,7 +202,7 @@ def test_split_production_error_table(F):
     if out:
         with open(out, "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
-    for L in (2048, 4096):
+    for L in (1024, 2048, 4096):
         for name in ("fp32", "fp16", "bf16x3"):
             assert table["L%d_%s" % (L, name)]["max_abs"] < 1e-3, (L, name, table)
         # the two-part BF16 form: its own bound only (a known miss of 1e-3)
