@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched / refinement / split-precision measurements")
     ap.add_argument("--batch-trials", type=int, default=256)
-    ap.add_argument("--rows", default="a8,a9,f1,f2,f3,f4,a11,a10",
+    ap.add_argument("--rows", default="a2,a8,a9,f1,f2,f3,f4,a11,a10",
                     help="scope rows measured after the timed steps (comma list)")
     ap.add_argument("--prec", type=int, default=0, choices=[0, 1, 2, 3],
                     help="DFT arithmetic of the timed step: 0 FP32, 1 FP16 hi+lo, 2 BF16 hi+lo, "
@@ -330,6 +330,44 @@ def batched_row(args, torch, dev):
             "autotune": tune, "autotune_s": t_tune,
             "launch": "one CUDA graph: bank + %d front ends + %d persistent convolver launches"
                       % (ntr, len(bs.waves))}
+
+
+def frontend_row(args, torch, dev, S, wl):
+    """fdas_normalise alone (real FFT + block-median normalisation) at the
+    production length and at other lengths, powers of two and not (Bluestein):
+    time per call with L2 flushed before each, and the series read plus the
+    spectrum write (8 bytes per sample, the floor of any front end) against
+    the measured HBM peak."""
+    from paper_1804_05335_gb300 import fdas_normalise, fdas_normalise_workspace_bytes
+    peak, _ = measured_peak()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(11)
+    res = {}
+    for n in (1 << 23, 1 << 22, 1 << 20, 2 * int(round(2.0 ** 21.5)), 2 * int(round(2.0 ** 22.3))):
+        x = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+        spec = torch.empty(n // 2, dtype=torch.complex64, device=dev)
+        wb = fdas_normalise_workspace_bytes(n)
+        work = torch.empty(wb, dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            fdas_normalise(x, n, wl.median_block, spec, work, wb)
+        ms = []
+        for _ in range(20):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fdas_normalise(x, n, wl.median_block, spec, work, wb)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        floor_bytes = 8 * n
+        res[str(n)] = {"ms": t, "power_of_two": not (n & (n - 1)),
+                       "floor_bytes": floor_bytes,
+                       "floor_gbs": floor_bytes / (t / 1e3) / 1e9,
+                       "floor_frac_of_peak": floor_bytes / (t / 1e3) / 1e9 / peak,
+                       "floor_ms": floor_bytes / (peak * 1e9) * 1e3}
+        del x, spec, work
+    return {"median_block": wl.median_block, "lengths": res}
 
 
 def plane16_row(args, torch, dev, S, wl):
@@ -820,7 +858,8 @@ def run_native(args):
         if ws == 1 and not args.no_rows:
             want = set(args.rows.split(","))
             rows = {}
-            for key, name, fn in (("a8", "a8_threshold", threshold_row),
+            for key, name, fn in (("a2", "a2_frontend", frontend_row),
+                                  ("a8", "a8_threshold", threshold_row),
                                   ("a9", "a9_split", split_row), ("f1", "f1_plane16", plane16_row),
                                   ("f2", "f2_interp2", interp2_row),
                                   ("f3", "f3_harmonic", harmonic_row),

@@ -85,7 +85,7 @@ static void plan_groups(const fdas_params* p, Grid* g) {
     }
 }
 
-int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm) {
+int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm, int carveout) {
     static std::mutex mu;
     static std::map<std::pair<const void*, int>, std::pair<int, int>> done;
     int dev = 0;
@@ -96,6 +96,9 @@ int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm
         int n = 0, per = 0;
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
+            (carveout >= 0 &&
+             cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) !=
+                 cudaSuccess) ||
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess)
             return FDAS_E_CUDA;

@@ -192,36 +192,105 @@ constexpr float kW32s[16] = {0.0f, 0.19509032201612826785f, 0.382683432365089771
                              0.70710678118654752440f, 0.55557023301960222474f,
                              0.38268343236508977173f, 0.19509032201612826785f};
 
-// v * w32^K,  w32 = exp(S i 2 pi / 32),  0 <= K < 16 a compile-time constant
+// Butterfly (a, b) -> (a + w b, a - w b) with the compile-time twiddle
+// w = w32^K = exp(S i 2 pi K / 32), in three packed multiply-adds (the
+// tangent form of the butterfly, Linzer and Feig):
+//   |s| <= |c|:  w b = c u,    u = b + i (s/c) b,
+//   |s| >  |c|:  w b = i s u,  u = b - i (c/s) b,
+// u one multiply-add of the swapped pair, each output one more.  A product
+// followed by two additions takes four packed operations.  w = +-1, +-i:
+// two additions.
 template <int S, int K>
-__device__ __forceinline__ float2 w32(float2 v) {
-    if constexpr (K % 2 == 0) {
-        return w16<S, K / 2>(v);
+__device__ __forceinline__ void bfly32(float2& a, float2& b) {
+    constexpr int k = ((K % 32) + 32) % 32;
+    if constexpr (k == 0) {
+        const float2 t = a - b;
+        a = a + b;
+        b = t;
+    } else if constexpr (k == 16) {
+        const float2 t = a + b;
+        a = a - b;
+        b = t;
+    } else if constexpr (k == 8) {      // w = S i
+        const float2 t = sub_si<S>(a, b);
+        a = add_si<S>(a, b);
+        b = t;
+    } else if constexpr (k == 24) {     // w = -S i
+        const float2 t = add_si<S>(a, b);
+        a = sub_si<S>(a, b);
+        b = t;
     } else {
-        constexpr float c = kW32c[K], s = (float)S * kW32s[K];
-        return cmul_k(v, c, s);
+        constexpr float c = k < 16 ? kW32c[k] : -kW32c[k - 16];
+        constexpr float s = (float)S * (k < 16 ? kW32s[k] : -kW32s[k - 16]);
+        constexpr float ac = c < 0.f ? -c : c, as = s < 0.f ? -s : s;
+        const float2 bs = make_float2(b.y, b.x);
+        if constexpr (k % 8 == 4) {     // |c| = |s|: u = b +- i b, one addition
+            const float2 u = (s / c > 0.f) ? add_si<1>(b, b) : sub_si<1>(b, b);
+            const float2 x = __ffma2_rn(u, make_float2(c, c), a);
+            b = __ffma2_rn(u, make_float2(-c, -c), a);
+            a = x;
+        } else if constexpr (as <= ac) {
+            constexpr float t = s / c;
+            const float2 u = __ffma2_rn(bs, make_float2(-t, t), b);
+            const float2 x = __ffma2_rn(u, make_float2(c, c), a);
+            b = __ffma2_rn(u, make_float2(-c, -c), a);
+            a = x;
+        } else {
+            constexpr float ct = c / s;
+            const float2 u = __ffma2_rn(bs, make_float2(ct, -ct), b);
+            const float2 us = make_float2(u.y, u.x);
+            const float2 x = __ffma2_rn(us, make_float2(-s, s), a);
+            b = __ffma2_rn(us, make_float2(s, -s), a);
+            a = x;
+        }
     }
 }
 
-// Last radix-2 layer of the 32-point DFT: X[K] = E[K] + w^K O[K],
-// X[K+16] = E[K] - w^K O[K] for K = KK..15 (w^8 = S i folded into the adds).
-template <int S, int KK>
-__device__ __forceinline__ void dft32_combine(float2* v, const float2* e, const float2* o) {
-    if constexpr (KK < 16) {
-        if constexpr (KK == 8) {
-            v[8] = add_si<S>(e[8], o[8]);
-            v[24] = sub_si<S>(e[8], o[8]);
-        } else {
-            const float2 t = w32<S, KK>(o[KK]);
-            v[KK] = e[KK] + t;
-            v[KK + 16] = e[KK] - t;
-        }
-        dft32_combine<S, KK + 1>(v, e, o);
+// 16 points (n = 4 n1 + n2, k = k1 + 4 k2) in tangent-form butterflies: the
+// column DFTs over n1, then per row k1 the twiddles w16^(n2 k1) folded into
+// the row DFT: with b_n2 the row's values,
+//   (b0, b2) and (b1, b3) by w16^(2 k1)  -> (s02, d02), (q+, q-),
+//   (s02, q+) by w16^k1, (d02, q-) by S i w16^k1  -> X0, X2, X1, X3.
+// (w16^m = w32^(2m).)  74 packed operations against 80 for dft16.
+template <int S, int K1>
+__device__ __forceinline__ void dft16t_row(float2* b) {
+    bfly32<S, 4 * K1>(b[0], b[2]);       // s02, d02
+    bfly32<S, 4 * K1>(b[1], b[3]);       // q+, q-
+    bfly32<S, 2 * K1>(b[0], b[1]);       // X0, X2
+    bfly32<S, 2 * K1 + 8>(b[2], b[3]);   // X1, X3
+    const float2 x1 = b[2], x2 = b[1];
+    b[1] = x1;
+    b[2] = x2;
+}
+
+template <int S>
+__device__ __forceinline__ void dft16t(float2* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<S>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    dft16t_row<S, 0>(v);
+    dft16t_row<S, 1>(v + 4);
+    dft16t_row<S, 2>(v + 8);
+    dft16t_row<S, 3>(v + 12);
+    // X[k1 + 4 k2] sits in v[4 k1 + k2]: transpose the 4x4
+    float2 t;
+    t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[2]; v[2] = v[8]; v[8] = t;
+    t = v[3]; v[3] = v[12]; v[12] = t;
+    t = v[6]; v[6] = v[9]; v[9] = t;
+    t = v[7]; v[7] = v[13]; v[13] = t;
+    t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <int S, int K>
+__device__ __forceinline__ void dft32_combine(float2* e, float2* o) {
+    if constexpr (K < 16) {
+        bfly32<S, K>(e[K], o[K]);
+        dft32_combine<S, K + 1>(e, o);
     }
 }
 
 // 32 points in natural order: 16-point DFTs of the even and the odd inputs,
-// then one radix-2 layer.
+// then one radix-2 layer X[K] = E[K] + w32^K O[K], X[K + 16] = E[K] - w32^K O[K].
 template <int S>
 __device__ __forceinline__ void dft32(float2* v) {
     float2 e[16], o[16];
@@ -230,9 +299,14 @@ __device__ __forceinline__ void dft32(float2* v) {
         e[i] = v[2 * i];
         o[i] = v[2 * i + 1];
     }
-    dft16<S>(e);
-    dft16<S>(o);
-    dft32_combine<S, 0>(v, e, o);
+    dft16t<S>(e);
+    dft16t<S>(o);
+    dft32_combine<S, 0>(e, o);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = e[i];
+        v[i + 16] = o[i];
+    }
 }
 
 }  // namespace fdas

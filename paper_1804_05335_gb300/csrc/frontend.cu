@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "dft.cuh"
 #include "internal.h"
@@ -92,129 +93,159 @@ __device__ void tile_dft_r(float2* x, float2* y, const float2* tw) {
     __syncthreads();
 }
 
-__device__ float2* tile_dft(float2* x, float2* y, const float2* tw, int R) {
-    switch (R) {
-        case 16: tile_dft_r<1>(x, y, tw); break;
-        case 32: tile_dft_r<2>(x, y, tw); break;
-        case 64: tile_dft_r<4>(x, y, tw); break;
-        case 128: tile_dft_r<8>(x, y, tw); break;
-        default: tile_dft_r<16>(x, y, tw); break;
-    }
-    return x;
-}
-
-__device__ void load_tw(float2* tw, int R) {
+// tw[q] = exp(-i 2 pi q / R), q < R
+template <int R>
+__device__ __forceinline__ void load_tw(float2* tw) {
     for (int q = threadIdx.x; q < R; q += blockDim.x) {
         float s, c;
-        sincospif(2.0f * (float)q / (float)R, &s, &c);
+        sincospif((float)q * (2.0f / (float)R), &s, &c);
         tw[q] = make_float2(c, -s);
     }
 }
 
-// exp(-i 2 pi e / N) with 0 <= e < N (N a power of two, e exact in float)
-__device__ __forceinline__ float2 twiddle(int64_t e, int64_t N) {
+// exp(-i pi x) for x = 2 e / N given as an exact float (e < N <= 2^24, N a
+// power of two, so e * (2/N) is exact and no division is needed)
+__device__ __forceinline__ float2 twiddle_pi(float x) {
     float s, c;
-    sincospif(2.0f * (float)e / (float)N, &s, &c);
+    sincospif(x, &s, &c);
     return make_float2(c, -s);
 }
 
-// pass A: DFT over n3 (length N3, stride N12), 16 consecutive lines m per CTA
+// A pass over lines of R points (R = 16 .. 256, a compile-time constant):
+// each CTA of 256 threads moves 16 lines, thread t taking column t % 16 of
+// rows t / 16 + 16 s (passes A, B) or point t % R of lines t / R + (256/R) s
+// (pass C), s < R/16.  All R/16 loads are issued before the first store to
+// shared memory, so a thread keeps them in flight together.
+template <int R>
+struct FeLine {
+    static constexpr int R1 = R / 16;
+    static constexpr int PER = R / 16;        // values per thread
+};
+
+// pass A: DFT over n3 (length R = N3, stride N12), 16 consecutive lines m per
+// CTA; output k3 of line m times exp(-i 2 pi m k3 / N) (m k3 < N)
+template <int R>
 __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict__ in,
-                                                        float2* __restrict__ out, int N3,
-                                                        int64_t N12, int64_t N) {
+                                                        float2* __restrict__ out, int64_t N12,
+                                                        float two_over_n) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + N3;
-    float2* y = x + N3 * kTilePad;
-    const int64_t m0 = (int64_t)blockIdx.x * 16;
-    load_tw(tw, N3);
-    for (int idx = threadIdx.x; idx < 16 * N3; idx += blockDim.x) {
-        const int col = idx & 15, r = idx >> 4;
-        x[r * kTilePad + col] = in[m0 + col + r * N12];
-    }
+    float2* x = tw + R;
+    float2* y = x + R * kTilePad;
+    constexpr int PER = FeLine<R>::PER;
+    const int t = threadIdx.x, col = t & 15, rr = t >> 4;
+    const int64_t m = (int64_t)blockIdx.x * 16 + col;
+    float2 ld[PER];
+#pragma unroll
+    for (int s = 0; s < PER; ++s) ld[s] = __ldg(&in[m + (int64_t)(rr + 16 * s) * N12]);
+    load_tw<R>(tw);
+#pragma unroll
+    for (int s = 0; s < PER; ++s) x[(rr + 16 * s) * kTilePad + col] = ld[s];
     __syncthreads();
-    float2* res = tile_dft(x, y, tw, N3);
-    for (int idx = threadIdx.x; idx < 16 * N3; idx += blockDim.x) {
-        const int col = idx & 15, k3 = idx >> 4;
-        const int64_t m = m0 + col;
-        out[m + k3 * N12] = c_mul(res[k3 * kTilePad + col], twiddle((m * k3) % N, N));
+    tile_dft_r<FeLine<R>::R1>(x, y, tw);
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        const int k3 = rr + 16 * s;
+        out[m + k3 * N12] =
+            c_mul(x[k3 * kTilePad + col], twiddle_pi((float)(m * k3) * two_over_n));
     }
 }
 
-// pass B: DFT over n2 (length N2, stride N1), in place; 16 consecutive n1 per CTA
-__global__ void __launch_bounds__(kFeThreads) fe_pass_b(float2* __restrict__ buf, int N1, int N2) {
+// pass B: DFT over n2 (length R = N2, stride N1), in place; 16 consecutive
+// n1 per CTA; output k2 of line n1 times exp(-i 2 pi n1 k2 / (N1 N2))
+template <int R>
+__global__ void __launch_bounds__(kFeThreads) fe_pass_b(float2* __restrict__ buf, int N1,
+                                                        float two_over_n12) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + N2;
-    float2* y = x + N2 * kTilePad;
+    float2* x = tw + R;
+    float2* y = x + R * kTilePad;
+    constexpr int PER = FeLine<R>::PER;
     const int chunks = N1 / 16;
+    const int t = threadIdx.x, col = t & 15, rr = t >> 4;
     const int64_t k3 = blockIdx.x / chunks;
-    const int n10 = (blockIdx.x % chunks) * 16;
-    const int64_t N12 = (int64_t)N1 * N2;
-    const int64_t base = k3 * N12 + n10;
-    load_tw(tw, N2);
-    for (int idx = threadIdx.x; idx < 16 * N2; idx += blockDim.x) {
-        const int col = idx & 15, r = idx >> 4;
-        x[r * kTilePad + col] = buf[base + col + (int64_t)r * N1];
-    }
+    const int n1 = (blockIdx.x % chunks) * 16 + col;
+    const int64_t base = k3 * N1 * R + n1;
+    float2 ld[PER];
+#pragma unroll
+    for (int s = 0; s < PER; ++s) ld[s] = buf[base + (int64_t)(rr + 16 * s) * N1];
+    load_tw<R>(tw);
+#pragma unroll
+    for (int s = 0; s < PER; ++s) x[(rr + 16 * s) * kTilePad + col] = ld[s];
     __syncthreads();
-    float2* res = tile_dft(x, y, tw, N2);
-    for (int idx = threadIdx.x; idx < 16 * N2; idx += blockDim.x) {
-        const int col = idx & 15, k2 = idx >> 4;
-        const int64_t e = ((int64_t)(n10 + col) * k2) % N12;
-        buf[base + col + (int64_t)k2 * N1] = c_mul(res[k2 * kTilePad + col], twiddle(e, N12));
+    tile_dft_r<FeLine<R>::R1>(x, y, tw);
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        const int k2 = rr + 16 * s;
+        buf[base + (int64_t)k2 * N1] =
+            c_mul(x[k2 * kTilePad + col], twiddle_pi((float)(n1 * k2) * two_over_n12));
     }
 }
 
-// pass C: DFT over n1 (contiguous, length N1); 16 consecutive k3 per CTA,
+// pass C: DFT over n1 (contiguous, length R = N1); 16 consecutive k3 per CTA,
 // written to natural order X[k3 + N3 k2 + N3 N2 k1]
+template <int R>
 __global__ void __launch_bounds__(kFeThreads) fe_pass_c(const float2* __restrict__ in,
-                                                        float2* __restrict__ out, int N1, int N2,
-                                                        int N3) {
+                                                        float2* __restrict__ out, int N2, int N3) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
-    float2* x = tw + N1;
-    float2* y = x + N1 * kTilePad;
+    float2* x = tw + R;
+    float2* y = x + R * kTilePad;
+    constexpr int PER = FeLine<R>::PER;
     const int chunks = N3 / 16;
     const int64_t k2 = blockIdx.x / chunks;
     const int64_t k30 = (int64_t)(blockIdx.x % chunks) * 16;
-    const int64_t N12 = (int64_t)N1 * N2;
-    load_tw(tw, N1);
-    for (int idx = threadIdx.x; idx < 16 * N1; idx += blockDim.x) {
-        const int r = idx % N1, col = idx / N1;
-        x[r * kTilePad + col] = in[(k30 + col) * N12 + k2 * N1 + r];
-    }
+    const int64_t N12 = (int64_t)R * N2;
+    const int t = threadIdx.x, r = t % R, c0 = t / R;
+    float2 ld[PER];
+#pragma unroll
+    for (int s = 0; s < PER; ++s)
+        ld[s] = __ldg(&in[(k30 + c0 + (256 / R) * s) * N12 + k2 * R + r]);
+    load_tw<R>(tw);
+#pragma unroll
+    for (int s = 0; s < PER; ++s) x[r * kTilePad + c0 + (256 / R) * s] = ld[s];
     __syncthreads();
-    float2* res = tile_dft(x, y, tw, N1);
+    tile_dft_r<FeLine<R>::R1>(x, y, tw);
     const int64_t N32 = (int64_t)N3 * N2;
-    for (int idx = threadIdx.x; idx < 16 * N1; idx += blockDim.x) {
-        const int col = idx & 15, k1 = idx >> 4;
-        out[k30 + col + N3 * k2 + N32 * k1] = res[k1 * kTilePad + col];
+    const int col = t & 15, rr = t >> 4;
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        const int k1 = rr + 16 * s;
+        out[k30 + col + N3 * k2 + N32 * k1] = x[k1 * kTilePad + col];
     }
 }
 
-// Exact rank-`rank` element of keys[0..len) (unsigned order) by 8-bit radix
-// select; every thread of the CTA returns it.
-__device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32_t* hist,
-                                 int* bc) {
+// Exact rank-`rank` element of keys[0..len) (unsigned order, every key below
+// 2^31: non-negative floats) by radix select on bits 30-23, 22-15, 14-7, 6-0;
+// every thread of the CTA returns it.  The histograms and results alternate
+// between two buffers, so a round takes two barriers: the CTA counts the
+// keys that match the prefix into hist[r & 1]; then warp 0 scans it while the
+// other warps clear the next round's buffer.  hist[0] must be zero on entry.
+__device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32_t (*hist)[256],
+                                 int (*bc)[2]) {
     uint32_t prefix = 0, pmask = 0;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
+#pragma unroll 1
+    for (int round = 0; round < 4; ++round) {
+        const int shift = round < 3 ? 23 - 8 * round : 0;
+        const uint32_t dmask = round < 3 ? 255u : 127u;
+        uint32_t* h0 = hist[round & 1];
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
             const uint32_t k = keys[i];
-            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+            if ((k & pmask) == prefix) atomicAdd(&h0[(k >> shift) & dmask], 1u);
         }
         __syncthreads();
         if (threadIdx.x < 32) {
             const int l = threadIdx.x;
-            uint32_t h[8], sum = 0;
+            const uint4 a = reinterpret_cast<const uint4*>(h0)[2 * l];
+            const uint4 b = reinterpret_cast<const uint4*>(h0)[2 * l + 1];
+            const uint32_t h[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            uint32_t sum = 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) { h[e] = hist[8 * l + e]; sum += h[e]; }
+            for (int e = 0; e < 8; ++e) sum += h[e];
             uint32_t inc = sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
                 if (l >= o) inc += v;
             }
             const unsigned hit = __ballot_sync(0xffffffffu, inc > (uint32_t)rank);
@@ -227,25 +258,31 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
                     if (base + h[e] > (uint32_t)rank) { d = e; break; }
                     base += h[e];
                 }
-                bc[0] = 8 * l + d;
-                bc[1] = rank - (int)base;
+                bc[round & 1][0] = 8 * l + d;
+                bc[round & 1][1] = rank - (int)base;
             }
+        } else {
+            uint32_t* h1 = hist[(round + 1) & 1];
+            for (int i = threadIdx.x - 32; i < 256; i += blockDim.x - 32) h1[i] = 0;
         }
         __syncthreads();
-        const uint32_t dig = (uint32_t)bc[0];
-        rank = bc[1];
-        prefix |= dig << shift;
-        pmask |= 255u << shift;
-        __syncthreads();
+        rank = bc[round & 1][1];
+        prefix |= (uint32_t)bc[round & 1][0] << shift;
+        pmask |= dmask << shift;
     }
     return prefix;
 }
 
-// c_m = exp(-i pi m^2 / N) for 0 <= m < 2^24: m^2 mod 2N in integers, then FP32
-__device__ __forceinline__ float2 chirp(int64_t m, int64_t N) {
-    const int64_t r = (m * m) % (2 * N);
+// c_m = exp(-i pi m^2 / N) for 0 <= m < N <= 2^23: r = m^2 mod 2N exactly (a
+// float estimate of the quotient, within 2 of it, corrected in integers),
+// then the FP32 sine and cosine of pi r / N.
+__device__ __forceinline__ float2 chirp(int64_t m, int64_t N, float inv_2n, float inv_n) {
+    const int64_t two_n = 2 * N, sq = m * m;
+    int64_t r = sq - (int64_t)((float)sq * inv_2n) * two_n;
+    while (r < 0) r += two_n;
+    while (r >= two_n) r -= two_n;
     float s, c;
-    sincospif((float)r / (float)N, &s, &c);
+    sincospif((float)r * inv_n, &s, &c);
     return make_float2(c, -s);
 }
 
@@ -253,37 +290,39 @@ __device__ __forceinline__ float2 chirp(int64_t m, int64_t N) {
 // after Bluestein's convolution of length P, Z_k = c_k conj(D_k) / P.
 template <bool BLUE>
 __device__ __forceinline__ float2 z_value(const float2* __restrict__ D, int64_t k, int64_t N,
-                                          float inv_p) {
+                                          float inv_p, float inv_2n, float inv_n) {
     const float2 d = D[k];
     if constexpr (!BLUE) {
         return d;
     } else {
-        const float2 c = chirp(k, N);
+        const float2 c = chirp(k, N, inv_2n, inv_n);
         return make_float2(inv_p * fmaf(c.x, d.x, c.y * d.y), inv_p * fmaf(c.y, d.x, -c.x * d.y));
     }
 }
 
-// one CTA per median block: real-spectrum post-processing + normalisation
+// one CTA per median block: real-spectrum post-processing + normalisation.
+// inv_n = 1/N (exact for power-of-two N), inv_2n = 1/(2N).
 template <bool BLUE>
 __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__ Z,
                                                       float2* __restrict__ spec, int64_t N,
-                                                      int block, float inv_p) {
+                                                      int block, float inv_p, float inv_n,
+                                                      float inv_2n) {
     extern __shared__ float2 psm[];
     float2* xs = psm;
     uint32_t* keys = reinterpret_cast<uint32_t*>(xs + block);
-    __shared__ uint32_t hist[256];
-    __shared__ int bc[2];
+    __shared__ __align__(16) uint32_t hist[2][256];
+    __shared__ int bc[2][2];
     const int64_t k0 = (int64_t)blockIdx.x * block;
     const int len = (int)min((int64_t)block, N - k0);
-    const int64_t n = 2 * N;
+    hist[0][threadIdx.x] = 0;   // 256 threads
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const int64_t k = k0 + i;
-        const float2 zk = z_value<BLUE>(Z, k, N, inv_p);
-        const float2 zm = z_value<BLUE>(Z, k == 0 ? 0 : N - k, N, inv_p);
+        const float2 zk = z_value<BLUE>(Z, k, N, inv_p, inv_2n, inv_n);
+        const float2 zm = z_value<BLUE>(Z, k == 0 ? 0 : N - k, N, inv_p, inv_2n, inv_n);
         const float ex = 0.5f * (zk.x + zm.x), ey = 0.5f * (zk.y - zm.y);
         const float ox = 0.5f * (zk.y + zm.y), oy = -0.5f * (zk.x - zm.x);
         float s, c;
-        sincospif(2.0f * (float)k / (float)n, &s, &c);
+        sincospif((float)k * inv_n, &s, &c);   // 2 pi k / n = pi k / N
         // w = (c, -s):  X = E + w O
         float2 X = make_float2(ex + fmaf(c, ox, s * oy), ey + fmaf(c, oy, -s * ox));
         if (k == 0) X = make_float2(0.f, 0.f);
@@ -303,19 +342,20 @@ __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__
 // Bluestein inputs: a[m] = z_m c_m for m < N, 0 up to P
 __global__ void __launch_bounds__(kFeThreads) bs_chirp_in(const float2* __restrict__ z,
                                                           float2* __restrict__ a, int64_t N,
-                                                          int64_t P) {
+                                                          int64_t P, float inv_2n, float inv_n) {
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < P;
          m += (int64_t)gridDim.x * blockDim.x)
-        a[m] = m < N ? c_mul(z[m], chirp(m, N)) : make_float2(0.f, 0.f);
+        a[m] = m < N ? c_mul(z[m], chirp(m, N, inv_2n, inv_n)) : make_float2(0.f, 0.f);
 }
 
 // the convolution kernel conj(c_j), j in (-N, N), placed circularly in P
 __global__ void __launch_bounds__(kFeThreads) bs_chirp_kernel(float2* __restrict__ b, int64_t N,
-                                                              int64_t P) {
+                                                              int64_t P, float inv_2n,
+                                                              float inv_n) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = j < N ? j : (j > P - N ? P - j : -1);
-        const float2 c = d >= 0 ? chirp(d, N) : make_float2(0.f, 0.f);
+        const float2 c = d >= 0 ? chirp(d, N, inv_2n, inv_n) : make_float2(0.f, 0.f);
         b[j] = make_float2(c.x, -c.y);
     }
 }
@@ -347,31 +387,70 @@ static int64_t bluestein_length(int64_t n) {
     return P;
 }
 
-// The three-pass forward FFT of P points (a power of two, 2^12..2^24): in ->
-// out (natural order; out may be in), tmp holds P values in between.
-static int fft_pow2(const float2* in, float2* tmp, float2* out, int64_t P, cudaStream_t st) {
-    const int p = log2i(P);
+// f(std::integral_constant<int, R>) for the line length R = 16 .. 256
+template <class F>
+static int with_line(int R, F&& f) {
+    switch (R) {
+        case 16: return f(std::integral_constant<int, 16>{});
+        case 32: return f(std::integral_constant<int, 32>{});
+        case 64: return f(std::integral_constant<int, 64>{});
+        case 128: return f(std::integral_constant<int, 128>{});
+        case 256: return f(std::integral_constant<int, 256>{});
+        default: return FDAS_E_UNSUPPORTED;
+    }
+}
+
+// The three-pass forward FFT of N points (a power of two, 2^12 .. 2^24):
+// pass A in -> mid, pass B in place in mid, pass C mid -> out (natural
+// order; out may be in).
+static int fft3(const float2* in, float2* mid, float2* out, int64_t N, cudaStream_t st) {
+    const int p = log2i(N);
     const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
     const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
     const int64_t N12 = (int64_t)N1 * N2;
-    fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(in, tmp, N3, N12, P);
-    fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(tmp, N1, N2);
-    fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(tmp, out, N1, N2,
-                                                                             N3);
-    return cuda_status(cudaGetLastError());
+    // powers of two: exact
+    const float two_over_n = 2.0f / (float)N, two_over_n12 = 2.0f / (float)N12;
+    int rc = with_line(N3, [&](auto r) {
+        constexpr int R = decltype(r)::value;
+        fe_pass_a<R><<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(R), st>>>(in, mid, N12,
+                                                                               two_over_n);
+        return FDAS_OK;
+    });
+    if (rc == FDAS_OK)
+        rc = with_line(N2, [&](auto r) {
+            constexpr int R = decltype(r)::value;
+            fe_pass_b<R><<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(R), st>>>(
+                mid, N1, two_over_n12);
+            return FDAS_OK;
+        });
+    if (rc == FDAS_OK)
+        rc = with_line(N1, [&](auto r) {
+            constexpr int R = decltype(r)::value;
+            fe_pass_c<R><<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(R), st>>>(mid, out,
+                                                                                       N2, N3);
+            return FDAS_OK;
+        });
+    return rc != FDAS_OK ? rc : cuda_status(cudaGetLastError());
 }
 
 static int frontend_setup() {
-    const size_t tile_sm = tile_bytes(256);   // the largest line (attribute)
     const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
-    int rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a), tile_sm, kFeThreads, nullptr,
-                          nullptr);
-    if (rc == FDAS_OK)
-        rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b), tile_sm, kFeThreads, nullptr,
-                          nullptr);
-    if (rc == FDAS_OK)
-        rc = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c), tile_sm, kFeThreads, nullptr,
-                          nullptr);
+    int rc = FDAS_OK;
+    for (int R = 16; R <= 256 && rc == FDAS_OK; R *= 2) {
+        rc = with_line(R, [&](auto r) {
+            constexpr int RR = decltype(r)::value;
+            // the carveout at its maximum: a pass is limited by CTAs resident
+            int q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a<RR>), tile_bytes(RR),
+                                 kFeThreads, nullptr, nullptr, 100);
+            if (q == FDAS_OK)
+                q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b<RR>), tile_bytes(RR),
+                                 kFeThreads, nullptr, nullptr, 100);
+            if (q == FDAS_OK)
+                q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c<RR>), tile_bytes(RR),
+                                 kFeThreads, nullptr, nullptr, 100);
+            return q;
+        });
+    }
     if (rc == FDAS_OK)
         rc = kernel_setup(reinterpret_cast<const void*>(&fe_post<false>), post_max, kFeThreads,
                           nullptr, nullptr);
@@ -410,17 +489,12 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     const float2* z = reinterpret_cast<const float2*>(series);
     const int nblk = (int)((N + median_block - 1) / median_block);
     const size_t post_sm = (size_t)median_block * (sizeof(float2) + sizeof(uint32_t));
+    const float inv_n = 1.0f / (float)N, inv_2n = 0.5f / (float)N;
     if (!(n & (n - 1))) {
         // power of two: the N-point FFT through the spectrum buffer into the workspace
-        const int p = log2i(N);
-        const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
-        const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
-        const int64_t N12 = (int64_t)N1 * N2;
-        fe_pass_a<<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(N3), st>>>(z, sp, N3, N12, N);
-        fe_pass_b<<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(N2), st>>>(sp, N1, N2);
-        fe_pass_c<<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(N1), st>>>(sp, wk, N1, N2,
-                                                                                 N3);
-        fe_post<false><<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block, 1.f);
+        if ((rc = fft3(z, sp, wk, N, st)) != FDAS_OK) return rc;
+        fe_post<false><<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block, 1.f, inv_n,
+                                                          inv_2n);
         return cuda_status(cudaGetLastError());
     }
     // Bluestein: workspace = [X | Bk | tmp], P complex each
@@ -429,15 +503,16 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     float2* Bk = wk + P;
     float2* tmp = wk + 2 * P;
     const unsigned grid = (unsigned)std::min<int64_t>((P + kFeThreads - 1) / kFeThreads, 152 * 16);
-    bs_chirp_in<<<grid, kFeThreads, 0, st>>>(z, X, N, P);
-    bs_chirp_kernel<<<grid, kFeThreads, 0, st>>>(Bk, N, P);
+    bs_chirp_in<<<grid, kFeThreads, 0, st>>>(z, X, N, P, inv_2n, inv_n);
+    bs_chirp_kernel<<<grid, kFeThreads, 0, st>>>(Bk, N, P, inv_2n, inv_n);
     if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
-    if ((rc = fft_pow2(X, tmp, X, P, st)) != FDAS_OK) return rc;
-    if ((rc = fft_pow2(Bk, tmp, Bk, P, st)) != FDAS_OK) return rc;
+    if ((rc = fft3(X, tmp, X, P, st)) != FDAS_OK) return rc;
+    if ((rc = fft3(Bk, tmp, Bk, P, st)) != FDAS_OK) return rc;
     bs_mul_conj<<<grid, kFeThreads, 0, st>>>(X, Bk, P);
     if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
-    if ((rc = fft_pow2(X, tmp, X, P, st)) != FDAS_OK) return rc;
-    fe_post<true><<<nblk, kFeThreads, post_sm, st>>>(X, sp, N, median_block, 1.0f / (float)P);
+    if ((rc = fft3(X, tmp, X, P, st)) != FDAS_OK) return rc;
+    fe_post<true><<<nblk, kFeThreads, post_sm, st>>>(X, sp, N, median_block, 1.0f / (float)P,
+                                                     inv_n, inv_2n);
     return cuda_status(cudaGetLastError());
 }
 

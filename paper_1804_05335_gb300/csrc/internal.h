@@ -56,7 +56,9 @@ inline bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)
 // dynamic shared memory for kernel `fn`, and report the device's SM count and
 // how many CTAs of `threads` threads with that shared memory fit on one SM.
 // FDAS_OK, FDAS_E_CUDA, or FDAS_E_UNSUPPORTED when not even one CTA fits.
-int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm);
+// carveout >= 0: also the preferred shared-memory carveout (percent), set once
+int kernel_setup(const void* fn, size_t smem, int threads, int* sms, int* per_sm,
+                 int carveout = -1);
 
 // Launchers implemented in the .cu files.
 int launch_templates(const fdas_params* p, const Grid& g, float2* bank, cudaStream_t st);
