@@ -122,12 +122,17 @@ struct FeLine {
     static constexpr int PER = R / 16;        // values per thread
 };
 
+// Inputs of pass A: src(j) is the j-th value of the FFT's input.
+struct SrcPlain {   // a stored array
+    const float2* a;
+    __device__ __forceinline__ float2 operator()(int64_t j) const { return __ldg(&a[j]); }
+};
+
 // pass A: DFT over n3 (length R = N3, stride N12), 16 consecutive lines m per
 // CTA; output k3 of line m times exp(-i 2 pi m k3 / N) (m k3 < N)
-template <int R>
-__global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict__ in,
-                                                        float2* __restrict__ out, int64_t N12,
-                                                        float two_over_n) {
+template <int R, class Src>
+__global__ void __launch_bounds__(kFeThreads) fe_pass_a(const Src src, float2* __restrict__ out,
+                                                        int64_t N12, float two_over_n) {
     extern __shared__ float2 fsm[];
     float2* tw = fsm;
     float2* x = tw + R;
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_a(const float2* __restrict
     const int64_t m = (int64_t)blockIdx.x * 16 + col;
     float2 ld[PER];
 #pragma unroll
-    for (int s = 0; s < PER; ++s) ld[s] = __ldg(&in[m + (int64_t)(rr + 16 * s) * N12]);
+    for (int s = 0; s < PER; ++s) ld[s] = src(m + (int64_t)(rr + 16 * s) * N12);
     load_tw<R>(tw);
 #pragma unroll
     for (int s = 0; s < PER; ++s) x[(rr + 16 * s) * kTilePad + col] = ld[s];
@@ -215,13 +220,16 @@ __global__ void __launch_bounds__(kFeThreads) fe_pass_c(const float2* __restrict
     }
 }
 
-// Exact rank-`rank` element of keys[0..len) (unsigned order, every key below
-// 2^31: non-negative floats) by radix select on bits 30-23, 22-15, 14-7, 6-0;
-// every thread of the CTA returns it.  The histograms and results alternate
-// between two buffers, so a round takes two barriers: the CTA counts the
-// keys that match the prefix into hist[r & 1]; then warp 0 scans it while the
-// other warps clear the next round's buffer.  hist[0] must be zero on entry.
-__device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32_t (*hist)[256],
+// Exact rank-`rank` element of the CTA's keys (unsigned order, every key
+// below 2^31: non-negative floats), KPT per thread in registers (keys past
+// the block hold 0xffffffff and match no prefix), by radix select on bits
+// 30-23, 22-15, 14-7, 6-0; every thread of the CTA returns it.  The
+// histograms and results alternate between two buffers, so a round takes two
+// barriers: the CTA counts the keys that match the prefix into hist[r & 1];
+// then warp 0 scans it while the other warps clear the next round's buffer.
+// hist[0] must be zero (and visible to all threads) on entry.
+template <int KPT>
+__device__ uint32_t radix_select(const uint32_t (&key)[KPT], int rank, uint32_t (*hist)[256],
                                  int (*bc)[2]) {
     uint32_t prefix = 0, pmask = 0;
 #pragma unroll 1
@@ -229,10 +237,10 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
         const int shift = round < 3 ? 23 - 8 * round : 0;
         const uint32_t dmask = round < 3 ? 255u : 127u;
         uint32_t* h0 = hist[round & 1];
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t k = keys[i];
-            if ((k & pmask) == prefix) atomicAdd(&h0[(k >> shift) & dmask], 1u);
-        }
+#pragma unroll
+        for (int s = 0; s < KPT; ++s)
+            if ((key[s] & pmask) == prefix && key[s] != 0xffffffffu)
+                atomicAdd(&h0[(key[s] >> shift) & dmask], 1u);
         __syncthreads();
         if (threadIdx.x < 32) {
             const int l = threadIdx.x;
@@ -262,8 +270,9 @@ __device__ uint32_t radix_select(const uint32_t* keys, int len, int rank, uint32
                 bc[round & 1][1] = rank - (int)base;
             }
         } else {
-            uint32_t* h1 = hist[(round + 1) & 1];
-            for (int i = threadIdx.x - 32; i < 256; i += blockDim.x - 32) h1[i] = 0;
+            // threads 32..255 clear bins 32..255, threads 32..63 also bins 0..31
+            hist[(round + 1) & 1][threadIdx.x] = 0;
+            if (threadIdx.x < 64) hist[(round + 1) & 1][threadIdx.x - 32] = 0;
         }
         __syncthreads();
         rank = bc[round & 1][1];
@@ -300,77 +309,100 @@ __device__ __forceinline__ float2 z_value(const float2* __restrict__ D, int64_t 
     }
 }
 
-// one CTA per median block: real-spectrum post-processing + normalisation.
-// inv_n = 1/N (exact for power-of-two N), inv_2n = 1/(2N).
-template <bool BLUE>
+// one CTA of 256 threads per median block (at most 256 KPT bins):
+// real-spectrum post-processing + normalisation.  Thread t takes bins
+// k0 + t + 256 s, s < KPT, kept in registers.  inv_n = 1/N (exact for
+// power-of-two N), inv_2n = 1/(2N).
+template <bool BLUE, int KPT>
 __global__ void __launch_bounds__(kFeThreads) fe_post(const float2* __restrict__ Z,
                                                       float2* __restrict__ spec, int64_t N,
                                                       int block, float inv_p, float inv_n,
                                                       float inv_2n) {
-    extern __shared__ float2 psm[];
-    float2* xs = psm;
-    uint32_t* keys = reinterpret_cast<uint32_t*>(xs + block);
     __shared__ __align__(16) uint32_t hist[2][256];
     __shared__ int bc[2][2];
     const int64_t k0 = (int64_t)blockIdx.x * block;
     const int len = (int)min((int64_t)block, N - k0);
     hist[0][threadIdx.x] = 0;   // 256 threads
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const int64_t k = k0 + i;
-        const float2 zk = z_value<BLUE>(Z, k, N, inv_p, inv_2n, inv_n);
-        const float2 zm = z_value<BLUE>(Z, k == 0 ? 0 : N - k, N, inv_p, inv_2n, inv_n);
-        const float ex = 0.5f * (zk.x + zm.x), ey = 0.5f * (zk.y - zm.y);
-        const float ox = 0.5f * (zk.y + zm.y), oy = -0.5f * (zk.x - zm.x);
-        float s, c;
-        sincospif((float)k * inv_n, &s, &c);   // 2 pi k / n = pi k / N
-        // w = (c, -s):  X = E + w O
-        float2 X = make_float2(ex + fmaf(c, ox, s * oy), ey + fmaf(c, oy, -s * ox));
-        if (k == 0) X = make_float2(0.f, 0.f);
-        xs[i] = X;
-        keys[i] = __float_as_uint(fmaf(X.x, X.x, X.y * X.y));
+    float2 X[KPT];
+    uint32_t key[KPT];
+#pragma unroll
+    for (int s = 0; s < KPT; ++s) {
+        const int i = threadIdx.x + kFeThreads * s;
+        X[s] = make_float2(0.f, 0.f);
+        key[s] = 0xffffffffu;
+        if (i < len) {
+            const int64_t k = k0 + i;
+            const float2 zk = z_value<BLUE>(Z, k, N, inv_p, inv_2n, inv_n);
+            const float2 zm = z_value<BLUE>(Z, k == 0 ? 0 : N - k, N, inv_p, inv_2n, inv_n);
+            const float ex = 0.5f * (zk.x + zm.x), ey = 0.5f * (zk.y - zm.y);
+            const float ox = 0.5f * (zk.y + zm.y), oy = -0.5f * (zk.x - zm.x);
+            float sn, cs;
+            sincospif((float)k * inv_n, &sn, &cs);   // 2 pi k / n = pi k / N
+            // w = (cs, -sn):  X = E + w O
+            if (k != 0) X[s] = make_float2(ex + fmaf(cs, ox, sn * oy), ey + fmaf(cs, oy, -sn * ox));
+            key[s] = __float_as_uint(fmaf(X[s].x, X[s].x, X[s].y * X[s].y));
+        }
     }
     __syncthreads();
-    const uint32_t mk = radix_select(keys, len, (len - 1) / 2, hist, bc);
+    const uint32_t mk = radix_select<KPT>(key, (len - 1) / 2, hist, bc);
     const float med = __uint_as_float(mk);
     const float scale = med > 0.f ? sqrtf(0.69314718055994531f / med) : 0.f;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const float2 X = xs[i];
-        spec[k0 + i] = make_float2(X.x * scale, X.y * scale);
+#pragma unroll
+    for (int s = 0; s < KPT; ++s) {
+        const int i = threadIdx.x + kFeThreads * s;
+        if (i < len) spec[k0 + i] = make_float2(X[s].x * scale, X[s].y * scale);
     }
 }
 
-// Bluestein inputs: a[m] = z_m c_m for m < N, 0 up to P
-__global__ void __launch_bounds__(kFeThreads) bs_chirp_in(const float2* __restrict__ z,
-                                                          float2* __restrict__ a, int64_t N,
-                                                          int64_t P, float inv_2n, float inv_n) {
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < P;
-         m += (int64_t)gridDim.x * blockDim.x)
-        a[m] = m < N ? c_mul(z[m], chirp(m, N, inv_2n, inv_n)) : make_float2(0.f, 0.f);
+// The post kernel for median blocks of `block` bins (32 .. 8192)
+template <bool BLUE>
+static int launch_post(const float2* Z, float2* spec, int64_t N, int block, float inv_p,
+                       float inv_n, float inv_2n, cudaStream_t st) {
+    const int nblk = (int)((N + block - 1) / block);
+    const int kpt = (block + kFeThreads - 1) / kFeThreads;
+    auto go = [&](auto kk) {
+        constexpr int K = decltype(kk)::value;
+        fe_post<BLUE, K><<<nblk, kFeThreads, 0, st>>>(Z, spec, N, block, inv_p, inv_n, inv_2n);
+        return cuda_status(cudaGetLastError());
+    };
+    if (kpt <= 1) return go(std::integral_constant<int, 1>{});
+    if (kpt <= 2) return go(std::integral_constant<int, 2>{});
+    if (kpt <= 4) return go(std::integral_constant<int, 4>{});
+    if (kpt <= 8) return go(std::integral_constant<int, 8>{});
+    if (kpt <= 16) return go(std::integral_constant<int, 16>{});
+    return go(std::integral_constant<int, 32>{});
 }
 
-// the convolution kernel conj(c_j), j in (-N, N), placed circularly in P
-__global__ void __launch_bounds__(kFeThreads) bs_chirp_kernel(float2* __restrict__ b, int64_t N,
-                                                              int64_t P, float inv_2n,
-                                                              float inv_n) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
-         j += (int64_t)gridDim.x * blockDim.x) {
+// Bluestein's three FFT inputs, generated inside pass A of each FFT:
+// a[m] = z_m c_m (m < N, then zeros up to P) ...
+struct SrcChirpIn {
+    const float2* z;
+    int64_t N;
+    float inv_2n, inv_n;
+    __device__ __forceinline__ float2 operator()(int64_t m) const {
+        return m < N ? c_mul(__ldg(&z[m]), chirp(m, N, inv_2n, inv_n)) : make_float2(0.f, 0.f);
+    }
+};
+// ... the convolution kernel conj(c_j), j in (-N, N), placed circularly in P ...
+struct SrcChirpKernel {
+    int64_t N, P;
+    float inv_2n, inv_n;
+    __device__ __forceinline__ float2 operator()(int64_t j) const {
         const int64_t d = j < N ? j : (j > P - N ? P - j : -1);
         const float2 c = d >= 0 ? chirp(d, N, inv_2n, inv_n) : make_float2(0.f, 0.f);
-        b[j] = make_float2(c.x, -c.y);
+        return make_float2(c.x, -c.y);
     }
-}
-
-// x = conj(x y): the product of the two spectra, conjugated so that a forward
-// FFT of it gives the conjugated inverse
-__global__ void __launch_bounds__(kFeThreads) bs_mul_conj(float2* __restrict__ x,
-                                                          const float2* __restrict__ y,
-                                                          int64_t P) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const float2 p = c_mul(x[k], y[k]);
-        x[k] = make_float2(p.x, -p.y);
+};
+// ... and conj(A B), the product of the two spectra conjugated, so that a
+// forward FFT of it gives the conjugated inverse.
+struct SrcProductConj {
+    const float2* a;
+    const float2* b;
+    __device__ __forceinline__ float2 operator()(int64_t k) const {
+        const float2 p = c_mul(a[k], b[k]);
+        return make_float2(p.x, -p.y);
     }
-}
+};
 
 static int log2i(int64_t v) {
     int p = 0;
@@ -401,9 +433,10 @@ static int with_line(int R, F&& f) {
 }
 
 // The three-pass forward FFT of N points (a power of two, 2^12 .. 2^24):
-// pass A in -> mid, pass B in place in mid, pass C mid -> out (natural
-// order; out may be in).
-static int fft3(const float2* in, float2* mid, float2* out, int64_t N, cudaStream_t st) {
+// pass A src -> mid, pass B in place in mid, pass C mid -> out (natural
+// order).
+template <class Src>
+static int fft3(const Src& src, float2* mid, float2* out, int64_t N, cudaStream_t st) {
     const int p = log2i(N);
     const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
     const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
@@ -412,13 +445,19 @@ static int fft3(const float2* in, float2* mid, float2* out, int64_t N, cudaStrea
     const float two_over_n = 2.0f / (float)N, two_over_n12 = 2.0f / (float)N12;
     int rc = with_line(N3, [&](auto r) {
         constexpr int R = decltype(r)::value;
-        fe_pass_a<R><<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(R), st>>>(in, mid, N12,
-                                                                               two_over_n);
+        const int q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a<R, Src>),
+                                   tile_bytes(R), kFeThreads, nullptr, nullptr, 100);
+        if (q != FDAS_OK) return q;
+        fe_pass_a<R, Src><<<(unsigned)(N12 / 16), kFeThreads, tile_bytes(R), st>>>(src, mid, N12,
+                                                                                    two_over_n);
         return FDAS_OK;
     });
     if (rc == FDAS_OK)
         rc = with_line(N2, [&](auto r) {
             constexpr int R = decltype(r)::value;
+            const int q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b<R>), tile_bytes(R),
+                                       kFeThreads, nullptr, nullptr, 100);
+            if (q != FDAS_OK) return q;
             fe_pass_b<R><<<(unsigned)(N3 * (N1 / 16)), kFeThreads, tile_bytes(R), st>>>(
                 mid, N1, two_over_n12);
             return FDAS_OK;
@@ -426,38 +465,14 @@ static int fft3(const float2* in, float2* mid, float2* out, int64_t N, cudaStrea
     if (rc == FDAS_OK)
         rc = with_line(N1, [&](auto r) {
             constexpr int R = decltype(r)::value;
+            const int q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c<R>), tile_bytes(R),
+                                       kFeThreads, nullptr, nullptr, 100);
+            if (q != FDAS_OK) return q;
             fe_pass_c<R><<<(unsigned)(N2 * (N3 / 16)), kFeThreads, tile_bytes(R), st>>>(mid, out,
                                                                                        N2, N3);
             return FDAS_OK;
         });
     return rc != FDAS_OK ? rc : cuda_status(cudaGetLastError());
-}
-
-static int frontend_setup() {
-    const size_t post_max = 8192 * (sizeof(float2) + sizeof(uint32_t));
-    int rc = FDAS_OK;
-    for (int R = 16; R <= 256 && rc == FDAS_OK; R *= 2) {
-        rc = with_line(R, [&](auto r) {
-            constexpr int RR = decltype(r)::value;
-            // the carveout at its maximum: a pass is limited by CTAs resident
-            int q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_a<RR>), tile_bytes(RR),
-                                 kFeThreads, nullptr, nullptr, 100);
-            if (q == FDAS_OK)
-                q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_b<RR>), tile_bytes(RR),
-                                 kFeThreads, nullptr, nullptr, 100);
-            if (q == FDAS_OK)
-                q = kernel_setup(reinterpret_cast<const void*>(&fe_pass_c<RR>), tile_bytes(RR),
-                                 kFeThreads, nullptr, nullptr, 100);
-            return q;
-        });
-    }
-    if (rc == FDAS_OK)
-        rc = kernel_setup(reinterpret_cast<const void*>(&fe_post<false>), post_max, kFeThreads,
-                          nullptr, nullptr);
-    if (rc == FDAS_OK)
-        rc = kernel_setup(reinterpret_cast<const void*>(&fe_post<true>), post_max, kFeThreads,
-                          nullptr, nullptr);
-    return rc;
 }
 
 }  // namespace fdas
@@ -482,38 +497,26 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     if (!aligned(series, 8) || !aligned(spec, 8) || !aligned(work, 16)) return FDAS_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = n / 2;
-    int rc = frontend_setup();
-    if (rc != FDAS_OK) return rc;
+    int rc = FDAS_OK;
     float2* sp = reinterpret_cast<float2*>(spec);
     float2* wk = reinterpret_cast<float2*>(work);
     const float2* z = reinterpret_cast<const float2*>(series);
-    const int nblk = (int)((N + median_block - 1) / median_block);
-    const size_t post_sm = (size_t)median_block * (sizeof(float2) + sizeof(uint32_t));
     const float inv_n = 1.0f / (float)N, inv_2n = 0.5f / (float)N;
     if (!(n & (n - 1))) {
         // power of two: the N-point FFT through the spectrum buffer into the workspace
-        if ((rc = fft3(z, sp, wk, N, st)) != FDAS_OK) return rc;
-        fe_post<false><<<nblk, kFeThreads, post_sm, st>>>(wk, sp, N, median_block, 1.f, inv_n,
-                                                          inv_2n);
-        return cuda_status(cudaGetLastError());
+        if ((rc = fft3(SrcPlain{z}, sp, wk, N, st)) != FDAS_OK) return rc;
+        return launch_post<false>(wk, sp, N, median_block, 1.f, inv_n, inv_2n, st);
     }
-    // Bluestein: workspace = [X | Bk | tmp], P complex each
+    // Bluestein: workspace = [X | Bk | tmp], P complex each; each FFT's input
+    // is generated in its first pass
     const int64_t P = bluestein_length(n);
     float2* X = wk;
     float2* Bk = wk + P;
     float2* tmp = wk + 2 * P;
-    const unsigned grid = (unsigned)std::min<int64_t>((P + kFeThreads - 1) / kFeThreads, 152 * 16);
-    bs_chirp_in<<<grid, kFeThreads, 0, st>>>(z, X, N, P, inv_2n, inv_n);
-    bs_chirp_kernel<<<grid, kFeThreads, 0, st>>>(Bk, N, P, inv_2n, inv_n);
-    if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
-    if ((rc = fft3(X, tmp, X, P, st)) != FDAS_OK) return rc;
-    if ((rc = fft3(Bk, tmp, Bk, P, st)) != FDAS_OK) return rc;
-    bs_mul_conj<<<grid, kFeThreads, 0, st>>>(X, Bk, P);
-    if ((rc = cuda_status(cudaGetLastError())) != FDAS_OK) return rc;
-    if ((rc = fft3(X, tmp, X, P, st)) != FDAS_OK) return rc;
-    fe_post<true><<<nblk, kFeThreads, post_sm, st>>>(X, sp, N, median_block, 1.0f / (float)P,
-                                                     inv_n, inv_2n);
-    return cuda_status(cudaGetLastError());
+    if ((rc = fft3(SrcChirpIn{z, N, inv_2n, inv_n}, tmp, X, P, st)) != FDAS_OK) return rc;
+    if ((rc = fft3(SrcChirpKernel{N, P, inv_2n, inv_n}, tmp, Bk, P, st)) != FDAS_OK) return rc;
+    if ((rc = fft3(SrcProductConj{X, Bk}, tmp, X, P, st)) != FDAS_OK) return rc;
+    return launch_post<true>(X, sp, N, median_block, 1.0f / (float)P, inv_n, inv_2n, st);
 }
 
 }  // extern "C"
