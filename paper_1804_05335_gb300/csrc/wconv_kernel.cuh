@@ -582,15 +582,15 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float4 h = hr[j * 33 + l];
-                    v[2 * j] = cmul(Y[2 * j], make_float2(h.x, h.y));
-                    v[2 * j + 1] = cmul(Y[2 * j + 1], make_float2(h.z, h.w));
+                    v[2 * j] = cmul_p(Y[2 * j], make_float2(h.x, h.y));
+                    v[2 * j + 1] = cmul_p(Y[2 * j + 1], make_float2(h.z, h.w));
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float4 h = hr[527 - 33 * j - l];
-                    v[2 * j] = cmulc(Y[2 * j], make_float2(h.z, h.w));
-                    v[2 * j + 1] = cmulc(Y[2 * j + 1], make_float2(h.x, h.y));
+                    v[2 * j] = cmulc_p(Y[2 * j], make_float2(h.z, h.w));
+                    v[2 * j + 1] = cmulc_p(Y[2 * j + 1], make_float2(h.x, h.y));
                 }
             }
             // ---- inverse FFT ----

@@ -86,8 +86,8 @@ __device__ __forceinline__ void wfft_inverse(float2* v, float2* xb, const float4
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const float4 t = tw4[j * 32 + l];
-                if (j) v[2 * j] = cmul(v[2 * j], make_float2(t.x, t.y));
-                v[2 * j + 1] = cmul(v[2 * j + 1], make_float2(t.z, t.w));
+                if (j) v[2 * j] = cmul_p(v[2 * j], make_float2(t.x, t.y));
+                v[2 * j + 1] = cmul_p(v[2 * j + 1], make_float2(t.z, t.w));
             }
             wfft_transpose(v, xb, l);
         }
