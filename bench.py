@@ -317,6 +317,17 @@ def batched_row(args, torch, dev):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # the same work outside the graph, split into the front ends (bank + every
+    # trial's fdas_normalise) and the convolver waves
+    f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    f0.record()
+    bs.front()
+    f1.record()
+    for k in range(len(bs.waves)):
+        bs.correlate_wave(k)
+    f2.record()
+    torch.cuda.synchronize()
+    split = {"front_ms": f0.elapsed_time(f1), "waves_ms": f1.elapsed_time(f2)}
     cands, counts = bs.candidates()
     na = np.asarray(ns)
     pow2 = int(np.sum((na & (na - 1)) == 0))
@@ -326,6 +337,8 @@ def batched_row(args, torch, dev):
                       "powers_of_two": pow2, "total_samples": int(na.sum())},
             "waves": len(bs.waves), "plane_points": bs.plane_points,
             "ms_per_batch": ms, "points_per_s": bs.plane_points / (ms / 1e3),
+            "ungraphed_split": split,
+            "bluestein_spectra_bytes": int(bs.chirps.numel()) if bs.chirp_off else 0,
             "candidates": int(sum(len(v[0]) for v in cands.values())),
             "autotune": tune, "autotune_s": t_tune,
             "launch": "one CUDA graph: bank + %d front ends + %d persistent convolver launches"

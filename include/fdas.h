@@ -209,6 +209,41 @@ size_t fdas_normalise_workspace_bytes(int64_t n);
 int fdas_normalise(const float *series, int64_t n, int32_t median_block, float *spec,
                    void *work, size_t work_bytes, void *stream);
 
+/* Bytes of the Bluestein kernel spectrum for a series of n samples: P
+ * complex values (P the least power of two >= n - 1) for an even n that is
+ * not a power of two and that fdas_normalise accepts, else 0. */
+size_t fdas_bluestein_bytes(int64_t n);
+
+/*
+ * fdas_bluestein_prepare -- the input-independent part of fdas_normalise's
+ * Bluestein convolution for n samples (N = n/2): the spectrum
+ *   B = FFT_P(b),  b_j = conj(c_j) for 0 <= j < N, b_{P-j} = conj(c_j) for
+ *   0 < j < N, zeros between,  c_j = exp(-i pi j^2 / N),
+ * the same values fdas_normalise computes on every call.  Like an FFT
+ * library's plan: computed once per length and passed to every
+ * fdas_normalise_prepared call for that length, it removes one of the
+ * three P-point FFTs from each call.
+ * chirp_spec: (device) fdas_bluestein_bytes(n) bytes, 16-byte aligned;
+ *   written.  work: (device) fdas_normalise_workspace_bytes(n) bytes,
+ *   16-byte aligned, scratch.
+ * Errors: FDAS_E_INVAL (NULL or misaligned pointers, n a power of two or
+ *   unsupported, work_bytes too small).
+ */
+int fdas_bluestein_prepare(int64_t n, void *chirp_spec, void *work, size_t work_bytes,
+                           void *stream);
+
+/*
+ * fdas_normalise_prepared -- fdas_normalise with the Bluestein kernel
+ * spectrum supplied (from fdas_bluestein_prepare for the same n); the
+ * results are bit-identical to fdas_normalise's.  For a power-of-two n
+ * chirp_spec is not read (may be NULL) and the call is fdas_normalise.
+ * Other arguments, layout and errors as fdas_normalise; FDAS_E_INVAL also
+ * for a NULL or misaligned chirp_spec when n is not a power of two.
+ */
+int fdas_normalise_prepared(const float *series, int64_t n, int32_t median_block, float *spec,
+                            void *work, size_t work_bytes, const void *chirp_spec,
+                            void *stream);
+
 /* Largest series length fdas_normalise_noalloc accepts (2^20 samples). */
 #define FDAS_NOALLOC_MAX_N (1 << 20)
 

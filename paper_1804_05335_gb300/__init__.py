@@ -16,6 +16,7 @@ __all__ = [
     "params", "fdas_strerror", "fdas_version", "fdas_half_width", "fdas_num_templates",
     "fdas_bank_rows", "fdas_bank_floats", "fdas_num_segments", "fdas_plane_width", "fdas_make_templates",
     "fdas_normalise_workspace_bytes", "fdas_normalise", "fdas_normalise_noalloc",
+    "fdas_bluestein_bytes", "fdas_bluestein_prepare", "fdas_normalise_prepared",
     "fdas_correlate", "fdas_correlate_split", "fdas_threshold", "FDAS_NOALLOC_MAX_N",
     "fdas_debug_wait_timeout",
     "fdas_template_groups", "FDAS_MAX_GROUPS",
@@ -114,6 +115,10 @@ def load_library():
         "fdas_normalise_workspace_bytes": (c_sz, [c_i64]),
         "fdas_normalise": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]),
         "fdas_normalise_noalloc": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp]),
+        "fdas_bluestein_bytes": (c_sz, [c_i64]),
+        "fdas_bluestein_prepare": (ctypes.c_int, [c_i64, c_vp, c_vp, c_sz, c_vp]),
+        "fdas_normalise_prepared": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp,
+                                                   c_vp]),
         "fdas_correlate": (ctypes.c_int, [P(fdas_params), c_vp, c_i64, c_vp, c_vp, c_i64,
                                           P(fdas_fused_threshold), c_vp, c_vp]),
         "fdas_correlate_split": (ctypes.c_int, [P(fdas_params), c_i32, c_vp, c_i64, c_vp, c_vp,
@@ -250,6 +255,26 @@ def fdas_normalise(series, n: int, median_block: int, spec, work, work_bytes: in
     _check(load_library().fdas_normalise(_ptr(series), int(n), int(median_block), _ptr(spec),
                                          _ptr(work), int(work_bytes), _stream(stream)),
            "fdas_normalise")
+
+
+def fdas_bluestein_bytes(n: int) -> int:
+    return int(load_library().fdas_bluestein_bytes(int(n)))
+
+
+def fdas_bluestein_prepare(n: int, chirp_spec, work, work_bytes: int, stream=None) -> None:
+    """chirp_spec: device buffer of fdas_bluestein_bytes(n) bytes (written)."""
+    _check(load_library().fdas_bluestein_prepare(int(n), _ptr(chirp_spec), _ptr(work),
+                                                 int(work_bytes), _stream(stream)),
+           "fdas_bluestein_prepare")
+
+
+def fdas_normalise_prepared(series, n: int, median_block: int, spec, work, work_bytes: int,
+                            chirp_spec, stream=None) -> None:
+    """fdas_normalise with the Bluestein kernel spectrum from fdas_bluestein_prepare."""
+    _check(load_library().fdas_normalise_prepared(_ptr(series), int(n), int(median_block),
+                                                  _ptr(spec), _ptr(work), int(work_bytes),
+                                                  _ptr(chirp_spec), _stream(stream)),
+           "fdas_normalise_prepared")
 
 
 def fdas_normalise_noalloc(series, n: int, median_block: int, spec, stream=None) -> None:

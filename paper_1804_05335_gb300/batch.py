@@ -14,16 +14,17 @@ import ctypes
 import numpy as np
 import torch
 
-from . import (fdas_bank_floats, fdas_batch_plan, fdas_correlate_batched, fdas_fused_threshold,
-               fdas_make_templates, fdas_normalise, fdas_normalise_workspace_bytes,
-               fdas_num_templates, fdas_plane_width, fdas_trial, params)
+from . import (fdas_bank_floats, fdas_batch_plan, fdas_bluestein_bytes, fdas_bluestein_prepare,
+               fdas_correlate_batched, fdas_fused_threshold, fdas_make_templates,
+               fdas_normalise, fdas_normalise_prepared, fdas_normalise_workspace_bytes, fdas_num_templates,
+               fdas_plane_width, fdas_trial, params)
 
 
 class BatchSearch:
     def __init__(self, ns, L: int, M: int, zmin: int, zmax: int, zstep: int, interbin: int = 1,
                  median_block: int = 1024, thr: float = 20.0, cap_per_wave: int = 1 << 16,
                  pool_bytes: int = 32 << 30, ctas_per_sm: int = 0, templates_per_block: int = 0,
-                 device="cuda"):
+                 prepare_chirps: bool = True, device="cuda"):
         self.ns = [int(n) for n in ns]
         self.p = params(L, M, zmin, zmax, zstep, interbin)
         self.K = fdas_num_templates(self.p)
@@ -45,6 +46,20 @@ class BatchSearch:
         self.spec = torch.empty(int(self.b_off[-1]), dtype=torch.complex64, device=dev)
         self.work_bytes = max(fdas_normalise_workspace_bytes(n) for n in self.ns)
         self.work = torch.empty(self.work_bytes, dtype=torch.uint8, device=dev)
+        # Bluestein kernel spectra, one per distinct length that is not a power
+        # of two, computed once here (input-independent) and read by every run
+        self.chirp_off = {}
+        if prepare_chirps:
+            off = 0
+            for n in sorted(set(self.ns)):
+                cb = fdas_bluestein_bytes(n)
+                if cb:
+                    self.chirp_off[n] = off
+                    off += cb
+            self.chirps = torch.empty(max(off, 16), dtype=torch.uint8, device=dev)
+            for n, o in self.chirp_off.items():
+                fdas_bluestein_prepare(n, int(self.chirps.data_ptr()) + o, self.work,
+                                       self.work_bytes)
         self.bank = torch.empty(fdas_bank_floats(self.p), dtype=torch.float32, device=dev)
         # waves: consecutive trials whose planes fit the pool
         sizes = [self.K * st * 4 for st in self.strides]
@@ -105,9 +120,18 @@ class BatchSearch:
     def front(self, stream=None) -> None:
         fdas_make_templates(self.p, self.bank, stream)
         for i, n in enumerate(self.ns):
-            fdas_normalise(int(self.series.data_ptr()) + 4 * int(self.s_off[i]), n,
-                           self.median_block, int(self.spec.data_ptr()) + 8 * int(self.b_off[i]),
-                           self.work, self.work_bytes, stream)
+            chirp = (int(self.chirps.data_ptr()) + self.chirp_off[n]) if n in self.chirp_off else None
+            if chirp is None and (n & (n - 1)):
+                # no prepared spectrum: fdas_normalise computes it itself
+                fdas_normalise(int(self.series.data_ptr()) + 4 * int(self.s_off[i]), n,
+                               self.median_block,
+                               int(self.spec.data_ptr()) + 8 * int(self.b_off[i]),
+                               self.work, self.work_bytes, stream)
+                continue
+            fdas_normalise_prepared(int(self.series.data_ptr()) + 4 * int(self.s_off[i]), n,
+                                    self.median_block,
+                                    int(self.spec.data_ptr()) + 8 * int(self.b_off[i]),
+                                    self.work, self.work_bytes, chirp, stream)
 
     def correlate_wave(self, k: int, stream=None) -> None:
         fdas_correlate_batched(self.p, self.wave_tables[k], len(self.waves[k]),

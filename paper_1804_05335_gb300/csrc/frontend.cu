@@ -488,13 +488,36 @@ size_t fdas_normalise_workspace_bytes(int64_t n) {
     return P ? (size_t)(3 * P) * sizeof(float2) : 0;
 }
 
-int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* spec, void* work,
-                   size_t work_bytes, void* stream) {
+size_t fdas_bluestein_bytes(int64_t n) {
+    return (size_t)bluestein_length(n) * sizeof(float2);
+}
+
+int fdas_bluestein_prepare(int64_t n, void* chirp_spec, void* work, size_t work_bytes,
+                           void* stream) {
+    const int64_t P = bluestein_length(n);
+    if (!P || !chirp_spec || !work) return FDAS_E_INVAL;
+    if (work_bytes < fdas_normalise_workspace_bytes(n)) return FDAS_E_INVAL;
+    if (!aligned(chirp_spec, 16) || !aligned(work, 16)) return FDAS_E_INVAL;
+    const int64_t N = n / 2;
+    const float inv_n = 1.0f / (float)N, inv_2n = 0.5f / (float)N;
+    return fft3(SrcChirpKernel{N, P, inv_2n, inv_n}, reinterpret_cast<float2*>(work),
+                reinterpret_cast<float2*>(chirp_spec), P, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace fdas {
+// fdas_normalise (chirp_spec NULL: the Bluestein kernel spectrum computed
+// here) and fdas_normalise_prepared (supplied)
+static int normalise_impl(const float* series, int64_t n, int32_t median_block, float* spec,
+                          void* work, size_t work_bytes, const void* chirp_spec, void* stream) {
     if (!series || !spec || !work) return FDAS_E_INVAL;
     const size_t need = fdas_normalise_workspace_bytes(n);
     if (need == 0 || work_bytes < need) return FDAS_E_INVAL;
     if (median_block < 32 || median_block > 8192) return FDAS_E_INVAL;
     if (!aligned(series, 8) || !aligned(spec, 8) || !aligned(work, 16)) return FDAS_E_INVAL;
+    const bool pow2 = !(n & (n - 1));
+    if (!pow2 && chirp_spec && !aligned(chirp_spec, 16)) return FDAS_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = n / 2;
     int rc = FDAS_OK;
@@ -502,21 +525,40 @@ int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* 
     float2* wk = reinterpret_cast<float2*>(work);
     const float2* z = reinterpret_cast<const float2*>(series);
     const float inv_n = 1.0f / (float)N, inv_2n = 0.5f / (float)N;
-    if (!(n & (n - 1))) {
+    if (pow2) {
         // power of two: the N-point FFT through the spectrum buffer into the workspace
         if ((rc = fft3(SrcPlain{z}, sp, wk, N, st)) != FDAS_OK) return rc;
         return launch_post<false>(wk, sp, N, median_block, 1.f, inv_n, inv_2n, st);
     }
     // Bluestein: workspace = [X | Bk | tmp], P complex each; each FFT's input
-    // is generated in its first pass
+    // is generated in its first pass; Bk only when no prepared spectrum is given
     const int64_t P = bluestein_length(n);
     float2* X = wk;
     float2* Bk = wk + P;
     float2* tmp = wk + 2 * P;
     if ((rc = fft3(SrcChirpIn{z, N, inv_2n, inv_n}, tmp, X, P, st)) != FDAS_OK) return rc;
-    if ((rc = fft3(SrcChirpKernel{N, P, inv_2n, inv_n}, tmp, Bk, P, st)) != FDAS_OK) return rc;
-    if ((rc = fft3(SrcProductConj{X, Bk}, tmp, X, P, st)) != FDAS_OK) return rc;
+    const float2* B = reinterpret_cast<const float2*>(chirp_spec);
+    if (!B) {
+        if ((rc = fft3(SrcChirpKernel{N, P, inv_2n, inv_n}, tmp, Bk, P, st)) != FDAS_OK) return rc;
+        B = Bk;
+    }
+    if ((rc = fft3(SrcProductConj{X, B}, tmp, X, P, st)) != FDAS_OK) return rc;
     return launch_post<true>(X, sp, N, median_block, 1.0f / (float)P, inv_n, inv_2n, st);
+}
+}  // namespace fdas
+
+extern "C" {
+
+int fdas_normalise_prepared(const float* series, int64_t n, int32_t median_block, float* spec,
+                            void* work, size_t work_bytes, const void* chirp_spec,
+                            void* stream) {
+    if ((n & (n - 1)) && !chirp_spec) return FDAS_E_INVAL;
+    return normalise_impl(series, n, median_block, spec, work, work_bytes, chirp_spec, stream);
+}
+
+int fdas_normalise(const float* series, int64_t n, int32_t median_block, float* spec, void* work,
+                   size_t work_bytes, void* stream) {
+    return normalise_impl(series, n, median_block, spec, work, work_bytes, nullptr, stream);
 }
 
 }  // extern "C"

@@ -49,6 +49,13 @@ def test_host_helpers():
     assert F.fdas_normalise_workspace_bytes((1 << 24) - 2) == 3 * (1 << 24) * 8
     assert F.fdas_normalise_workspace_bytes(100001) == 0          # odd
     assert F.fdas_normalise_workspace_bytes((1 << 24) + 2) == 0   # past the largest convolution
+    # Bluestein kernel spectrum: P complex values for non-power-of-two lengths only
+    assert F.fdas_bluestein_bytes(100000) == (1 << 17) * 8
+    assert F.fdas_bluestein_bytes(8194) == (1 << 14) * 8
+    assert F.fdas_bluestein_bytes((1 << 24) - 2) == (1 << 24) * 8
+    assert F.fdas_bluestein_bytes(1 << 20) == 0
+    assert F.fdas_bluestein_bytes(100001) == 0
+    assert F.fdas_bluestein_bytes((1 << 24) + 2) == 0
     assert F.fdas_strerror(F.FDAS_E_INVAL) == "invalid argument"
 
 
@@ -85,6 +92,16 @@ def test_invalid_buffers_rejected_before_launch():
         lambda: F.fdas_normalise(256, 100000, 1024, 256, 256, 1 << 20, stream=0),  # work size
         lambda: F.fdas_normalise(256, 1 << 14, 16, 256, 256, 1 << 20, stream=0),   # block
         lambda: F.fdas_normalise(256, 1 << 14, 1024, 256, 256, 100, stream=0),     # work size
+        lambda: F.fdas_bluestein_prepare(1 << 20, 256, 256, 1 << 24, stream=0),    # power of two
+        lambda: F.fdas_bluestein_prepare(100000, 0, 256, 1 << 24, stream=0),       # NULL spectrum
+        lambda: F.fdas_bluestein_prepare(100000, 264, 256, 1 << 24, stream=0),     # misaligned
+        lambda: F.fdas_bluestein_prepare(100000, 256, 256, 1 << 20, stream=0),     # work size
+        lambda: F.fdas_normalise_prepared(256, 100000, 1024, 256, 256, 1 << 24, 0,
+                                          stream=0),                               # no spectrum
+        lambda: F.fdas_normalise_prepared(256, 100000, 1024, 256, 256, 1 << 24, 264,
+                                          stream=0),                               # misaligned
+        lambda: F.fdas_normalise_prepared(256, 100000, 1024, 256, 256, 1 << 20, 256,
+                                          stream=0),                               # work size
         lambda: F.fdas_threshold(256, 0, 10, 10, 20.0, 0, 256, 4, 256, stream=0),  # rows
         lambda: F.fdas_threshold(256, 3, 10, 9, 20.0, 0, 256, 4, 256, stream=0),   # stride
         lambda: F.fdas_threshold(256, 3, 10, 10, 20.0, 4, 256, 4, 256, stream=0),  # flags

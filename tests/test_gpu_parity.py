@@ -82,6 +82,28 @@ def test_normalise_matches_oracle(F, n, block, seed):
     assert got[0] == 0
 
 
+@pytest.mark.parametrize("n", [8194, 100000, 2 * 1234567, 1 << 16])
+def test_normalise_prepared_is_bit_identical(F, n):
+    """fdas_normalise_prepared with the kernel spectrum from
+    fdas_bluestein_prepare gives fdas_normalise's spectrum bit for bit (the
+    same FFT of the same chirp, computed once instead of per call); a power
+    of two needs no spectrum."""
+    x = torch.from_numpy(synth.make_series(n, ((n / 7 + 0.2, 6.0, 12.0),), 5)).cuda()
+    wb = F.fdas_normalise_workspace_bytes(n)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    a = torch.empty(n // 2, dtype=torch.complex64, device="cuda")
+    b = torch.full((n // 2,), float("nan"), dtype=torch.complex64, device="cuda")
+    F.fdas_normalise(x, n, 1024, a, work, wb)
+    cb = F.fdas_bluestein_bytes(n)
+    chirp = torch.empty(max(cb, 16), dtype=torch.uint8, device="cuda") if cb else None
+    if cb:
+        F.fdas_bluestein_prepare(n, chirp, work, wb)
+    work.fill_(0x7f)                      # the prepared call must not read stale scratch
+    F.fdas_normalise_prepared(x, n, 1024, b, work, wb, chirp)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.float32), b.view(torch.float32))
+
+
 def test_normalise_zero_series_gives_zero(F):
     n = 1 << 14
     S = _search(F, n=n, L=2048, M=256, zmin=0, zmax=0, zstep=1, plane=False)
