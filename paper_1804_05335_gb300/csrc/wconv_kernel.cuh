@@ -81,20 +81,26 @@ struct WSeries {
     __device__ __forceinline__ int flags() const { return 0; }
     __device__ __forceinline__ int trial() const { return 0; }
 };
+// (only the trial index and its last unit stay in registers; the other
+// fields are read from the trial table, an L1 hit, where they are used)
 template <>
 struct WSeries<true> {
-    SeriesState st;
     int tr;
+    int64_t last;   // first unit of the next trial
     __device__ __forceinline__ void set(const ConvArgs& A, int t) {
         tr = t;
-        st = series_of<true>(A, t);
+        last = (t + 1 < A.ntrials) ? A.trials[t + 1].item_begin : A.items;
     }
-    __device__ __forceinline__ const float2* spec(const ConvArgs&) const { return st.spec; }
-    __device__ __forceinline__ int64_t nb(const ConvArgs&) const { return st.nb; }
-    __device__ __forceinline__ float* plane(const ConvArgs&) const { return st.plane; }
-    __device__ __forceinline__ int64_t row_stride(const ConvArgs&) const { return st.row_stride; }
-    __device__ __forceinline__ int64_t end(const ConvArgs&) const { return st.end; }
-    __device__ __forceinline__ int flags() const { return st.flags; }
+    __device__ __forceinline__ const float2* spec(const ConvArgs& A) const {
+        return reinterpret_cast<const float2*>(A.trials[tr].spec);
+    }
+    __device__ __forceinline__ int64_t nb(const ConvArgs& A) const { return A.trials[tr].nb; }
+    __device__ __forceinline__ float* plane(const ConvArgs& A) const { return A.trials[tr].plane; }
+    __device__ __forceinline__ int64_t row_stride(const ConvArgs& A) const {
+        return A.trials[tr].row_stride;
+    }
+    __device__ __forceinline__ int64_t end(const ConvArgs&) const { return last; }
+    __device__ __forceinline__ int flags() const { return tr << 8; }
     __device__ __forceinline__ int trial() const { return tr; }
 };
 
