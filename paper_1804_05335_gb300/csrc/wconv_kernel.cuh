@@ -112,7 +112,7 @@ struct WSeries<true> {
 // all of the group's templates.
 template <bool BATCH, int SUB>
 struct WWalk {
-    int64_t u;        // unit index
+    int u;            // unit index
     WSeries<BATCH> ser;
     int nq;           // quads of group grp in the current series
     int quad;         // segments NW quad .. NW quad + NW - 1 of group grp
@@ -128,7 +128,7 @@ struct WWalk {
     __device__ __forceinline__ static int chunk(const ConvArgs& A, int g) {
         return (A.tpb > 0 && A.tpb < A.gK[g]) ? A.tpb : A.gK[g];
     }
-    __device__ __forceinline__ void init(const ConvArgs& A, int64_t u0) {
+    __device__ __forceinline__ void init(const ConvArgs& A, int u0) {
         u = u0;
         int trial = 0;
         if constexpr (BATCH) {   // last trial whose first unit is <= u0
@@ -411,8 +411,8 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
 
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     float2* xb = xall + w * WShape::XBUF;
-    const int64_t lo = (int64_t)blockIdx.x * A.items / gridDim.x;
-    const int64_t hi = (int64_t)(blockIdx.x + 1) * A.items / gridDim.x;
+    const int lo = (int)((int64_t)blockIdx.x * A.items / gridDim.x);
+    const int hi = (int)((int64_t)(blockIdx.x + 1) * A.items / gridDim.x);
     if (lo >= hi) return;
     const uint32_t limit = A.wait_limit ? A.wait_limit : kWaitLimit;   // copy-issuing thread
 
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
     float2 Y[32], v[32];
     bool fresh = true, live = false, fast = false;
     int cur_brow = -1, M2 = 0, B = 0, ilo = 0, ihi = 32;
-    int64_t r0 = 0, npos = 0;
+    int r0 = 0, npos = 0;
     uint32_t ri = 0xffffffffu;   // index of the row in use
     while (cw.u < hi) {
         int row, brow, cj;
@@ -527,8 +527,8 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
             // ---- a new quad: this warp's segment, its geometry and forward FFT ----
             M2 = A.gM[cw.grp] / 2;
             B = L - 2 * M2;
-            npos = cw.npos(A);
-            r0 = ((int64_t)cw.quad * NW + w) * B;   // bin of position M/2
+            npos = (int)cw.npos(A);
+            r0 = (cw.quad * NW + w) * B;   // bin of position M/2
             live = r0 < npos;
             fast = M2 <= 160 && r0 + B <= npos;
             ilo = (M2 - l + 31) >> 5;               // first register at position >= M/2
@@ -656,6 +656,9 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
 template <bool FUSE, bool BATCH, int OUT, int SUB, bool IB, int PREC = 0>
 static int launch_w(const ConvArgs& args, int ctas_per_sm, cudaStream_t st) {
     constexpr size_t smem = WSmem<PREC>::bytes;
+    // unit indices are 32-bit in the kernel (2^31 units of 4 segments would
+    // be a plane of more than 8 TB)
+    if (args.items > 0x7fffffff) return FDAS_E_UNSUPPORTED;
     int sms = 0, max_per_sm = 0;
     const int rc = kernel_setup(
         reinterpret_cast<const void*>(&wconv_kernel<FUSE, BATCH, OUT, SUB, IB, PREC>), smem,
