@@ -516,8 +516,8 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
     };
 
     float2 Y[32], v[32];
-    bool fresh = true, live = false, fast = false;
-    int cur_brow = -1, M2 = 0, B = 0, ilo = 0, ihi = 32;
+    bool fresh = true, live = false;
+    int cur_brow = -1, M2 = 0;
     int r0 = 0, npos = 0;
     uint32_t ri = 0xffffffffu;   // index of the row in use
     while (cw.u < hi) {
@@ -526,13 +526,10 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
         if (fresh) {
             // ---- a new quad: this warp's segment, its geometry and forward FFT ----
             M2 = A.gM[cw.grp] / 2;
-            B = L - 2 * M2;
+            const int B = L - 2 * M2;
             npos = (int)cw.npos(A);
             r0 = (cw.quad * NW + w) * B;   // bin of position M/2
             live = r0 < npos;
-            fast = M2 <= 160 && r0 + B <= npos;
-            ilo = (M2 - l + 31) >> 5;               // first register at position >= M/2
-            ihi = (L - M2 - l + 31) >> 5;           // first register at position >= M/2 + B
             if constexpr (PREC == 0) {
                 if (live) {
                     wseg_forward<SUB>(cw.ser.spec(A), cw.ser.nb(A), r0 - M2, xb, tw4, l);
@@ -614,8 +611,10 @@ __global__ void __launch_bounds__(WShape::NW * 32, PREC ? 2 : kWarpCtasPerSm)
                                   : static_cast<void*>(reinterpret_cast<uint16_t*>(cw.ser.plane(A)) +
                                                        (int64_t)row * cw.ser.row_stride(A));
             float mx;
-            if (fast) {
-                mx = wepi_fast<OUT, IB>(v, l, ilo, ihi, prow, r0 - M2 + l);
+            if (M2 <= 160 && r0 + L - 2 * M2 <= npos) {
+                // first registers at positions >= M/2 and >= M/2 + B
+                mx = wepi_fast<OUT, IB>(v, l, (M2 - l + 31) >> 5, (L - M2 - l + 31) >> 5, prow,
+                                        r0 - M2 + l);
             } else {
                 mx = wepi_staged<OUT, IB, false>(v, xb, l, M2, L - M2, r0, npos, prow, A, row, 0);
             }
