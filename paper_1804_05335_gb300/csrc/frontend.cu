@@ -12,7 +12,8 @@
 // Each pass moves tiles of 16 lines x R points through shared memory with
 // 128-byte coalesced rows and transforms each line by two register passes,
 // R = R1 x 16: radix R1 over every 16th point, a twiddle, one padded
-// transpose in shared memory, radix 16 (tile_dft).  A final kernel per median block forms the real spectrum
+// transpose in shared memory, radix 16 (tile_dft_r).  A final kernel per
+// median block forms the real spectrum
 //   X_k = E_k + exp(-i 2 pi k / n) O_k,  E = (Z_k + conj Z_{N-k})/2,
 //   O = (Z_k - conj Z_{N-k}) / 2i,   X_0 := 0,
 // selects the lower median of |X_k|^2 in the block exactly (radix select on
@@ -24,7 +25,10 @@
 // a linear convolution evaluated as a circular one of power-of-two length
 // P >= 2N - 1 with the three-pass FFT above: A = FFT(z c), B = FFT(conj c
 // placed circularly), D = FFT(conj(A B)), and Z_k = c_k conj(D_k) / P (the
-// inverse by conjugation).  m^2 is reduced modulo 2N in integers before the
+// inverse by conjugation).  Each FFT's input is generated inside its first
+// pass, and B, which depends only on n, can be computed once
+// (fdas_bluestein_prepare) and passed to every call for that length
+// (fdas_normalise_prepared).  m^2 is reduced modulo 2N in integers before the
 // FP32 sine and cosine, so the chirp's phase error stays at the rounding of
 // (m^2 mod 2N)/N.
 #include <math.h>
