@@ -68,11 +68,55 @@ __device__ __forceinline__ void harm_emit(const HarmArgs& A, int row, int64_t co
     }
 }
 
+// Sums and thresholds of a thread's fundamentals from their loaded
+// harmonics (nl[f] levels on the plane for fundamental f).
+__device__ __forceinline__ void harm_sums(const HarmArgs& A, int j, int64_t c0,
+                                          const float (&v)[kHarmPer][8], const int (&nl)[kHarmPer]) {
+#pragma unroll
+    for (int f = 0; f < kHarmPer; ++f) {
+        if (nl[f] == 0) continue;
+        const int64_t c = c0 + f * kHarmThreads;
+        float s = v[f][0] + v[f][1];
+        if (s > A.thr[0]) harm_emit(A, j, c, s, 2);
+        if (nl[f] < 2) continue;
+        s += v[f][2] + v[f][3];
+        if (s > A.thr[1]) harm_emit(A, j, c, s, 4);
+        if (nl[f] < 3) continue;
+        s += (v[f][4] + v[f][5]) + (v[f][6] + v[f][7]);
+        if (s > A.thr[2]) harm_emit(A, j, c, s, 8);
+    }
+}
+
+// A thread whose fundamentals all have NL levels on the plane: harmonic h of
+// fundamental f is element rowoff[h] + h c0 + h f 256, so each harmonic takes
+// one address and kHarmPer loads at fixed offsets from it.
+template <int TYPE, int NL>
+__device__ __forceinline__ void harm_block_full(const HarmArgs& A, int j, int64_t c0,
+                                                const int64_t (&rowoff)[8]) {
+    constexpr int H = 2 << (NL - 1);
+    float v[kHarmPer][8];
+    int nl[kHarmPer];
+#pragma unroll
+    for (int h = 1; h <= 8; ++h) {
+#pragma unroll
+        for (int f = 0; f < kHarmPer; ++f) {
+            v[f][h - 1] = 0.f;
+            if (h <= H) v[f][h - 1] = plane_load<TYPE>(A.plane, rowoff[h - 1] + (int64_t)h * c0 +
+                                                                    h * f * kHarmThreads);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < kHarmPer; ++f) nl[f] = NL;
+    harm_sums(A, j, c0, v, nl);
+}
+
 // One CTA: fundamentals c = blk * kHarmBlock + threadIdx.x + f * kHarmThreads
 // (f < kHarmPer) of fundamental row j.  Each thread issues every load of all
 // its fundamentals before forming the sums.  Harmonic rows j_h = h (j + j0h)
 // - j0h are linear in h, so the harmonics up to H are all on the plane when
-// j_H is.
+// j_H is; the levels whose columns are on the plane fall as c grows, so the
+// thread's fundamentals share their level count unless its first and last
+// differ.
 constexpr int kHarmBlock = kHarmThreads * kHarmPer;
 
 template <int TYPE>
@@ -87,14 +131,26 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
     int64_t rowoff[8];
 #pragma unroll
     for (int h = 1; h <= 8; ++h) rowoff[h - 1] = (int64_t)((h - 1) * A.j0h + h * j) * A.row_stride;
+    const int64_t c0 = blk * kHarmBlock + threadIdx.x;
+    auto levels = [&](int64_t c) {
+        int n = 0;   // levels whose columns are on the plane too
+        while (n < nlr && ((int64_t)2 << n) * c < A.width) ++n;
+        return n;
+    };
+    const int nfirst = levels(c0), nlast = levels(c0 + (kHarmPer - 1) * kHarmThreads);
+    if (nfirst == nlast) {   // the same levels for all of the thread's fundamentals
+        if (nlast == 3) harm_block_full<TYPE, 3>(A, j, c0, rowoff);
+        else if (nlast == 2) harm_block_full<TYPE, 2>(A, j, c0, rowoff);
+        else if (nlast == 1) harm_block_full<TYPE, 1>(A, j, c0, rowoff);
+        return;
+    }
+    // a level boundary falls between them: per-fundamental levels
     float v[kHarmPer][8];
     int nl[kHarmPer];
-    const int64_t c0 = blk * kHarmBlock + threadIdx.x;
 #pragma unroll
     for (int f = 0; f < kHarmPer; ++f) {
         const int64_t c = c0 + f * kHarmThreads;
-        int n = 0;   // levels whose columns are on the plane too
-        while (n < nlr && ((int64_t)2 << n) * c < A.width) ++n;
+        const int n = levels(c);
         nl[f] = n;
 #pragma unroll
         for (int h = 1; h <= 8; ++h) {
@@ -103,19 +159,7 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
             if (need <= n) v[f][h - 1] = plane_load<TYPE>(A.plane, rowoff[h - 1] + (int64_t)h * c);
         }
     }
-#pragma unroll
-    for (int f = 0; f < kHarmPer; ++f) {
-        if (nl[f] == 0) continue;
-        const int64_t c = c0 + f * kHarmThreads;
-        float s = v[f][0] + v[f][1];
-        if (s > A.thr[0]) harm_emit(A, j, c, s, 2);
-        if (nl[f] < 2) continue;
-        s += v[f][2] + v[f][3];
-        if (s > A.thr[1]) harm_emit(A, j, c, s, 4);
-        if (nl[f] < 3) continue;
-        s += (v[f][4] + v[f][5]) + (v[f][6] + v[f][7]);
-        if (s > A.thr[2]) harm_emit(A, j, c, s, 8);
-    }
+    harm_sums(A, j, c0, v, nl);
 }
 
 // Row-major order: x over groups of kRowPer column blocks, y over the
