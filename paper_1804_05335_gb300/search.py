@@ -72,11 +72,31 @@ class Search:
                        1 if want_peaks else 0, self.cand, self.cap, self.count, self.status,
                        stream)
 
-    def step(self, stream=None, series=None):
-        """One pass of the hot path: bank, spectrum, plane + fused candidates."""
-        self.make_templates(stream)
-        self.normalise(stream, series)
-        self.correlate(True, stream=stream, prec=self.prec)
+    def front(self, series=None):
+        """The template bank and the normalised spectrum, which do not depend on
+        each other: the bank is built on a second stream while the spectrum is
+        formed on the current one, which then waits for both.  Returns the
+        (start, end) events of the bank on its stream."""
+        main = torch.cuda.current_stream(self.device)
+        if not hasattr(self, "_side"):
+            self._side = torch.cuda.Stream(self.device)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        go = torch.cuda.Event()
+        go.record(main)
+        self._side.wait_event(go)
+        with torch.cuda.stream(self._side):
+            t0.record(self._side)
+            self.make_templates()
+            t1.record(self._side)
+        self.normalise(series=series)
+        main.wait_event(t1)
+        return t0, t1
+
+    def step(self, series=None):
+        """One pass of the hot path on the current stream: bank and spectrum
+        (overlapped, see front), plane + fused candidates."""
+        self.front(series)
+        self.correlate(True, prec=self.prec)
 
     def stream(self, host_series, host_out):
         """Search the pinned host series host_series[i] (n float32 each) one
@@ -103,8 +123,7 @@ class Search:
                 self._inbuf[j].copy_(hs, non_blocking=True)
                 loaded[j].record(self._copy)
             main.wait_event(loaded[j])
-            self.make_templates()
-            self.normalise(series=self._inbuf[j])
+            self.front(series=self._inbuf[j])
             free[j] = torch.cuda.Event()
             free[j].record(main)
             self.correlate(True, prec=self.prec)
