@@ -6,6 +6,7 @@ library next to this file.  Usage: ``python -m paper_1804_05335_gb300.build``.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import subprocess
@@ -40,7 +41,19 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link if the sources changed.  Processes that build at the
+    same time (one per rank) take turns on a lock file, so the object files
+    are never written by two compilers at once."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     stamp = os.path.join(OUT_DIR, "stamp")
     dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
