@@ -181,8 +181,8 @@ int64_t fdas_plane_width(const fdas_params *p, int64_t nb);
 int fdas_make_templates(const fdas_params *p, float *bank, void *stream);
 
 /* Workspace bytes fdas_normalise needs for n samples (0 if n unsupported):
- * n/2 complex values for a power of two, 3 P (P the least power of two
- * >= n - 1) for the other even lengths. */
+ * n/2 complex values for a power of two, 3 P for the other even lengths (P
+ * the least length >= n - 1 of the form 2^m or 3 * 2^m, 3 * 2^m <= 3 * 2^22). */
 size_t fdas_normalise_workspace_bytes(int64_t n);
 
 /*
@@ -198,7 +198,7 @@ size_t fdas_normalise_workspace_bytes(int64_t n);
  *   2^13 <= n <= 2^25, or any even n with 2^13 < n <= 2^24; the N = n/2
  *   point DFT of the packed samples then runs as Bluestein's chirp-z
  *   convolution, Z_k = c_k sum_m (z_m c_m) conj(c_{k-m}), c_m = exp(-i pi
- *   m^2/N), with power-of-two FFTs of length P >= n - 1.  median_block:
+ *   m^2/N), with FFTs of length P >= n - 1 (2^m or 3 * 2^m).  median_block:
  *   32..8192.
  * spec: (device) n/2 complex, written.
  * work: (device) fdas_normalise_workspace_bytes(n) bytes, 16-byte aligned;
@@ -210,8 +210,8 @@ int fdas_normalise(const float *series, int64_t n, int32_t median_block, float *
                    void *work, size_t work_bytes, void *stream);
 
 /* Bytes of the Bluestein kernel spectrum for a series of n samples: P
- * complex values (P the least power of two >= n - 1) for an even n that is
- * not a power of two and that fdas_normalise accepts, else 0. */
+ * complex values (P as in fdas_normalise_workspace_bytes) for an even n that
+ * is not a power of two and that fdas_normalise accepts, else 0. */
 size_t fdas_bluestein_bytes(int64_t n);
 
 /*

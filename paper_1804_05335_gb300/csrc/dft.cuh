@@ -145,6 +145,81 @@ __device__ __forceinline__ void dft8(float2* v) {
     v[6] = t5;
 }
 
+constexpr float kS3 = 0.86602540378443864676f;   // sin(pi/3) = sqrt(3)/2
+
+// 3 points: X1,2 = a - (b + c)/2 +- S i (sqrt3/2)(b - c)
+template <int S>
+__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
+    const float2 t1 = b + c;
+    const float2 t2 = __ffma2_rn(t1, make_float2(-0.5f, -0.5f), a);
+    const float2 d = __fmul2_rn(b - c, make_float2(kS3, kS3));
+    a = a + t1;
+    b = add_si<S>(t2, d);
+    c = sub_si<S>(t2, d);
+}
+
+// v * w^m, w = exp(S i 2 pi / 12), m a compile-time constant
+template <int S, int M>
+__device__ __forceinline__ float2 w12(float2 v) {
+    constexpr int m = ((M % 12) + 12) % 12;
+    if constexpr (m == 0) {
+        return v;
+    } else if constexpr (m == 3) {
+        return mul_si<S>(v);
+    } else if constexpr (m == 6) {
+        return make_float2(-v.x, -v.y);
+    } else if constexpr (m == 9) {
+        return mul_si<-S>(v);
+    } else {
+        // cos and sin of 2 pi m / 12 for m = 1, 2, 4, 5, 7, 8, 10, 11
+        constexpr float c = (m == 1 || m == 11) ? kS3 : (m == 2 || m == 10) ? 0.5f
+                          : (m == 4 || m == 8) ? -0.5f : -kS3;
+        constexpr float s0 = (m == 1 || m == 5) ? 0.5f : (m == 2 || m == 4) ? kS3
+                           : (m == 7 || m == 11) ? -0.5f : -kS3;
+        return cmul_k(v, c, (float)S * s0);
+    }
+}
+
+// 6 points in natural order: n = 2 n1 + n2, k = k1 + 3 k2
+template <int S>
+__device__ __forceinline__ void dft6(float2* v) {
+    dft3<S>(v[0], v[2], v[4]);
+    dft3<S>(v[1], v[3], v[5]);
+    const float2 e[3] = {v[0], v[2], v[4]};
+    const float2 o[3] = {v[1], w12<S, 2>(v[3]), w12<S, 4>(v[5])};
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        v[k1] = e[k1] + o[k1];
+        v[k1 + 3] = e[k1] - o[k1];
+    }
+}
+
+// 12 points in natural order: n = 4 n1 + n2, k = k1 + 3 k2; the 3-point DFTs
+// over n1, twiddles w12^(n2 k1), the 4-point DFTs over n2
+template <int S>
+__device__ __forceinline__ void dft12(float2* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft3<S>(v[n2], v[4 + n2], v[8 + n2]);
+    // v[n2 + 4 k1] = A[n2][k1]
+    float2 a[3][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) a[0][n2] = v[n2];
+    a[1][0] = v[4];
+    a[1][1] = w12<S, 1>(v[5]);
+    a[1][2] = w12<S, 2>(v[6]);
+    a[1][3] = w12<S, 3>(v[7]);
+    a[2][0] = v[8];
+    a[2][1] = w12<S, 2>(v[9]);
+    a[2][2] = w12<S, 4>(v[10]);
+    a[2][3] = w12<S, 6>(v[11]);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        dft4<S>(a[k1][0], a[k1][1], a[k1][2], a[k1][3]);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 3 * k2] = a[k1][k2];
+    }
+}
+
 // 16 points: n = 4 n1 + n2, k = k1 + 4 k2
 template <int S>
 __device__ __forceinline__ void dft16(float2* v) {

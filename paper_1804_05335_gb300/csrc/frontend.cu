@@ -3,8 +3,8 @@
 // DFT sign of Section 4.2).
 //
 // The n real samples are read as N = n/2 complex values z_m = x_2m + i x_2m+1
-// and transformed by a three-pass N-point FFT, N = N1 N2 N3 (each factor
-// 16..256):
+// and transformed by a three-pass N-point FFT, N = N1 N2 N3 (each factor a
+// power of two 16..256; N3 = 48, 96 or 192 for a Bluestein length 3 * 2^m):
 //   index n = n1 + N1 n2 + N1 N2 n3, frequency k = k3 + N3 k2 + N3 N2 k1;
 //   pass A: length-N3 DFTs over n3, twiddle exp(-i 2 pi (n1 + N1 n2) k3 / N);
 //   pass B: length-N2 DFTs over n2, twiddle exp(-i 2 pi n1 k2 / (N1 N2));
@@ -22,8 +22,8 @@
 // A series whose length n is even but not a power of two takes the N-point
 // DFT (N = n/2) by Bluestein's chirp-z identity: with c_m = exp(-i pi m^2/N),
 //   Z_k = sum_m z_m exp(-i 2 pi m k / N) = c_k sum_m (z_m c_m) conj(c_{k-m}),
-// a linear convolution evaluated as a circular one of power-of-two length
-// P >= 2N - 1 with the three-pass FFT above: A = FFT(z c), B = FFT(conj c
+// a linear convolution evaluated as a circular one of length P >= 2N - 1
+// (the least 2^m or 3 * 2^m) with the three-pass FFT above: A = FFT(z c), B = FFT(conj c
 // placed circularly), D = FFT(conj(A B)), and Z_k = c_k conj(D_k) / P (the
 // inverse by conjugation).  Each FFT's input is generated inside its first
 // pass, and B, which depends only on n, can be computed once
@@ -55,7 +55,8 @@ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Forward length-R DFT (R = R1*16) of the 16 columns of tile x[r*17 + col].
+// Forward length-R DFT (R = R1*16, R1 = 1, 2, 3, 4, 6, 8, 12, 16) of the 16
+// columns of tile x[r*17 + col].
 // Thread (col = t % 16, j = t / 16) takes points r = j + 16 i, i < R1, does
 // the radix-R1 DFT over i, multiplies output k1 by exp(-i 2 pi j k1 / R) and
 // stores it at y[(16 k1 + j)*17 + col]; thread (col, k1) then does the
@@ -71,6 +72,12 @@ __device__ void tile_dft_r(float2* x, float2* y, const float2* tw) {
         for (int i = 0; i < R1; ++i) v[i] = x[(jj + 16 * i) * kTilePad + col];
         if constexpr (R1 == 2) {
             dft2<-1>(v[0], v[1]);
+        } else if constexpr (R1 == 3) {
+            dft3<-1>(v[0], v[1], v[2]);
+        } else if constexpr (R1 == 6) {
+            dft6<-1>(v);
+        } else if constexpr (R1 == 12) {
+            dft12<-1>(v);
         } else if constexpr (R1 == 4) {
             dft4<-1>(v[0], v[1], v[2], v[3]);
         } else if constexpr (R1 == 8) {
@@ -415,20 +422,27 @@ static int log2i(int64_t v) {
 }
 
 // Bluestein convolution length for a series of n samples (n even, not a
-// power of two): the least power of two >= n - 1 = 2N - 1; 0 if out of range.
+// power of two): the least length >= n - 1 = 2N - 1 of the form 2^m or
+// 3 * 2^m (3 * 2^12 <= 3 * 2^m <= 3 * 2^22); 0 if n is out of range.
 static int64_t bluestein_length(int64_t n) {
     if (n < (1 << 13) || n > ((int64_t)1 << 24) || (n & 1) || !(n & (n - 1))) return 0;
     int64_t P = 1;
     while (P < n - 1) P <<= 1;
-    return P;
+    int64_t P3 = (int64_t)3 << 12;
+    while (P3 < n - 1) P3 <<= 1;
+    return (P3 < P && P3 <= ((int64_t)3 << 22)) ? P3 : P;
 }
 
-// f(std::integral_constant<int, R>) for the line length R = 16 .. 256
+// f(std::integral_constant<int, R>) for the line length R = 16 .. 256 (powers
+// of two, and 48, 96, 192 for pass A of a length 3 * 2^m)
 template <class F>
 static int with_line(int R, F&& f) {
     switch (R) {
         case 16: return f(std::integral_constant<int, 16>{});
         case 32: return f(std::integral_constant<int, 32>{});
+        case 48: return f(std::integral_constant<int, 48>{});
+        case 96: return f(std::integral_constant<int, 96>{});
+        case 192: return f(std::integral_constant<int, 192>{});
         case 64: return f(std::integral_constant<int, 64>{});
         case 128: return f(std::integral_constant<int, 128>{});
         case 256: return f(std::integral_constant<int, 256>{});
@@ -436,16 +450,32 @@ static int with_line(int R, F&& f) {
     }
 }
 
-// The three-pass forward FFT of N points (a power of two, 2^12 .. 2^24):
-// pass A src -> mid, pass B in place in mid, pass C mid -> out (natural
-// order).
+// The factors N = N1 N2 N3 of a transform length N = 2^m (2^12 .. 2^24) or
+// 3 * 2^m (3 * 2^12 .. 3 * 2^22): powers of two between 16 and 256, except
+// N3 = 3 * 2^a between 48 and 192 when 3 divides N.
+static void fft_factors(int64_t N, int& N1, int& N2, int& N3) {
+    const bool three = (N % 3) == 0;
+    const int p = log2i(three ? N / 3 : N);
+    int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
+    if (three) {
+        while (p3 > 6) {   // the pass A line 3 * 2^p3 stays <= 192
+            --p3;
+            if (p1 <= p2) ++p1; else ++p2;
+        }
+    }
+    N1 = 1 << p1;
+    N2 = 1 << p2;
+    N3 = (three ? 3 : 1) << p3;
+}
+
+// The three-pass forward FFT of N points (fft_factors): pass A src -> mid,
+// pass B in place in mid, pass C mid -> out (natural order).
 template <class Src>
 static int fft3(const Src& src, float2* mid, float2* out, int64_t N, cudaStream_t st) {
-    const int p = log2i(N);
-    const int p3 = p / 3, p2 = (p - p3) / 2, p1 = p - p2 - p3;
-    const int N1 = 1 << p1, N2 = 1 << p2, N3 = 1 << p3;
+    int N1, N2, N3;
+    fft_factors(N, N1, N2, N3);
     const int64_t N12 = (int64_t)N1 * N2;
-    // powers of two: exact
+    // 2/N12 is exact (a power of two), 2/N too unless 3 divides N
     const float two_over_n = 2.0f / (float)N, two_over_n12 = 2.0f / (float)N12;
     int rc = with_line(N3, [&](auto r) {
         constexpr int R = decltype(r)::value;

@@ -42,16 +42,20 @@ def test_host_helpers():
     assert [F.fdas_half_width(z) for z in (0, 1, -21, 200)] == [8, 9, 19, 108]
     assert F.fdas_normalise_workspace_bytes(1 << 23) == (1 << 22) * 8
     assert F.fdas_normalise_workspace_bytes(1000) == 0
-    # even lengths that are not powers of two: three buffers of the power-of-two
-    # convolution length P >= n - 1
+    # even lengths that are not powers of two: three buffers of the convolution
+    # length P >= n - 1, the least of the form 2^m or 3 * 2^m (m <= 22)
     assert F.fdas_normalise_workspace_bytes(100000) == 3 * (1 << 17) * 8
-    assert F.fdas_normalise_workspace_bytes(8194) == 3 * (1 << 14) * 8
+    assert F.fdas_normalise_workspace_bytes(8194) == 3 * (3 << 12) * 8
+    assert F.fdas_normalise_workspace_bytes(1048578) == 3 * (3 << 19) * 8
+    assert F.fdas_normalise_workspace_bytes(12290) == 3 * (1 << 14) * 8   # 12289 > 3 * 2^12
     assert F.fdas_normalise_workspace_bytes((1 << 24) - 2) == 3 * (1 << 24) * 8
     assert F.fdas_normalise_workspace_bytes(100001) == 0          # odd
     assert F.fdas_normalise_workspace_bytes((1 << 24) + 2) == 0   # past the largest convolution
     # Bluestein kernel spectrum: P complex values for non-power-of-two lengths only
     assert F.fdas_bluestein_bytes(100000) == (1 << 17) * 8
-    assert F.fdas_bluestein_bytes(8194) == (1 << 14) * 8
+    assert F.fdas_bluestein_bytes(8194) == (3 << 12) * 8
+    assert F.fdas_bluestein_bytes(6291458) == (1 << 23) * 8             # 3 * 2^21 < n - 1
+    assert F.fdas_bluestein_bytes(6291456) == (3 << 21) * 8
     assert F.fdas_bluestein_bytes((1 << 24) - 2) == (1 << 24) * 8
     assert F.fdas_bluestein_bytes(1 << 20) == 0
     assert F.fdas_bluestein_bytes(100001) == 0
