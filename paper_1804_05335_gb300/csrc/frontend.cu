@@ -114,15 +114,17 @@ __device__ __forceinline__ void load_tw(float2* tw) {
     }
 }
 
-// exp(-i pi x) for x = 2 e / N given as an exact float (e < N <= 2^24, N a
-// power of two, so e * (2/N) is exact and no division is needed)
+// exp(-i pi x) for x = 2 e / N given as a float (e < N <= 2^24 is exact in
+// float; e * (2/N) is exact for a power-of-two N and within half an ulp for
+// N = 3 * 2^m; no division is needed)
 __device__ __forceinline__ float2 twiddle_pi(float x) {
     float s, c;
     sincospif(x, &s, &c);
     return make_float2(c, -s);
 }
 
-// A pass over lines of R points (R = 16 .. 256, a compile-time constant):
+// A pass over lines of R points (R = 16 .. 256, a power of two, or 48, 96,
+// 192 for pass A; a compile-time constant):
 // each CTA of 256 threads moves 16 lines, thread t taking column t % 16 of
 // rows t / 16 + 16 s (passes A, B) or point t % R of lines t / R + (256/R) s
 // (pass C), s < R/16.  All R/16 loads are issued before the first store to
