@@ -115,7 +115,7 @@ __device__ __forceinline__ void load_tw(float2* tw) {
 }
 
 // exp(-i pi x) for x = 2 e / N given as a float (e < N <= 2^24 is exact in
-// float; e * (2/N) is exact for a power-of-two N and within half an ulp for
+// float; e * (2/N) is exact for a power-of-two N and within about an ulp for
 // N = 3 * 2^m; no division is needed)
 __device__ __forceinline__ float2 twiddle_pi(float x) {
     float s, c;
