@@ -64,6 +64,7 @@ def test_template_bank_matches_oracle(F, L, M, zmin, zmax, zstep):
 # ------------------------------------------------------------------ front end (a2-a3)
 @pytest.mark.parametrize("n,block,seed", [
     (1 << 13, 64, 3), (1 << 14, 1024, 4), (1 << 17, 1024, 1), (1 << 20, 1000, 5), (1 << 23, 1024, 2),
+    (1 << 25, 1024, 14),   # the largest length (three passes of 256-point lines)
     # even lengths that are not powers of two (Bluestein's convolution)
     (8194, 1024, 6), (3 << 12, 256, 7), (100000, 1024, 8), (1048578, 1024, 9), (5000002, 1024, 10),
     ((1 << 23) - 2, 1024, 11), ((1 << 24) - 2, 1024, 12),
