@@ -88,11 +88,12 @@ __device__ __forceinline__ void harm_sums(const HarmArgs& A, int j, int64_t c0,
 }
 
 // A thread whose fundamentals all have NL levels on the plane: harmonic h of
-// fundamental f is element rowoff[h] + h c0 + h f 256, so each harmonic takes
-// one address and kHarmPer loads at fixed offsets from it.
+// fundamental f is element h (ra + c0) - rb + h f 256 (the row offsets are
+// linear in h, ra and rb as in harm_block), so each harmonic takes one
+// address and kHarmPer loads at fixed offsets from it.
 template <int TYPE, int NL>
 __device__ __forceinline__ void harm_block_full(const HarmArgs& A, int j, int64_t c0,
-                                                const int64_t (&rowoff)[8]) {
+                                                int64_t ra, int64_t rb) {
     constexpr int H = 2 << (NL - 1);
     float v[kHarmPer][8];
     int nl[kHarmPer];
@@ -101,7 +102,7 @@ __device__ __forceinline__ void harm_block_full(const HarmArgs& A, int j, int64_
 #pragma unroll
         for (int f = 0; f < kHarmPer; ++f) {
             v[f][h - 1] = 0.f;
-            if (h <= H) v[f][h - 1] = plane_load<TYPE>(A.plane, rowoff[h - 1] + (int64_t)h * c0 +
+            if (h <= H) v[f][h - 1] = plane_load<TYPE>(A.plane, h * (ra + c0) - rb +
                                                                     h * f * kHarmThreads);
         }
     }
@@ -128,9 +129,8 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
         if (jH < 0 || jH >= A.K) break;
         nlr = lev + 1;
     }
-    int64_t rowoff[8];
-#pragma unroll
-    for (int h = 1; h <= 8; ++h) rowoff[h - 1] = (int64_t)((h - 1) * A.j0h + h * j) * A.row_stride;
+    // harmonic h's row starts at ((h - 1) j0h + h j) row_stride = h ra - rb
+    const int64_t ra = (int64_t)(A.j0h + j) * A.row_stride, rb = (int64_t)A.j0h * A.row_stride;
     const int64_t c0 = blk * kHarmBlock + threadIdx.x;
     auto levels = [&](int64_t c) {
         int n = 0;   // levels whose columns are on the plane too
@@ -139,9 +139,9 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
     };
     const int nfirst = levels(c0), nlast = levels(c0 + (kHarmPer - 1) * kHarmThreads);
     if (nfirst == nlast) {   // the same levels for all of the thread's fundamentals
-        if (nlast == 3) harm_block_full<TYPE, 3>(A, j, c0, rowoff);
-        else if (nlast == 2) harm_block_full<TYPE, 2>(A, j, c0, rowoff);
-        else if (nlast == 1) harm_block_full<TYPE, 1>(A, j, c0, rowoff);
+        if (nlast == 3) harm_block_full<TYPE, 3>(A, j, c0, ra, rb);
+        else if (nlast == 2) harm_block_full<TYPE, 2>(A, j, c0, ra, rb);
+        else if (nlast == 1) harm_block_full<TYPE, 1>(A, j, c0, ra, rb);
         return;
     }
     // a level boundary falls between them: per-fundamental levels
@@ -156,7 +156,7 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
         for (int h = 1; h <= 8; ++h) {
             const int need = h <= 2 ? 1 : (h <= 4 ? 2 : 3);
             v[f][h - 1] = 0.f;
-            if (need <= n) v[f][h - 1] = plane_load<TYPE>(A.plane, rowoff[h - 1] + (int64_t)h * c);
+            if (need <= n) v[f][h - 1] = plane_load<TYPE>(A.plane, h * (ra + c) - rb);
         }
     }
     harm_sums(A, j, c0, v, nl);
@@ -167,7 +167,11 @@ __device__ __forceinline__ void harm_block(const HarmArgs& A, int j, int64_t blk
 constexpr int kRowPer = 16;
 
 template <int TYPE>
-__global__ void __launch_bounds__(kHarmThreads) harmonic_kernel(const HarmArgs A, int jlo,
+// 6 CTAs per SM (at most 42 registers, a few bytes spilled): the kernels are held by
+// memory latency, and more warps keep more loads in flight (measured: 4 CTAs
+// 0.98 ms, 5 CTAs 0.81 ms, 6 CTAs 0.80 ms, 8 CTAs 0.87 ms planned on the FP32
+// production plane)
+__global__ void __launch_bounds__(kHarmThreads, 6) harmonic_kernel(const HarmArgs A, int jlo,
                                                                 int64_t nblk) {
     for (int g = 0; g < kRowPer; ++g) {
         const int64_t blk = (int64_t)blockIdx.x * kRowPer + g;
@@ -183,7 +187,7 @@ constexpr int kPlanHeaderWords = 16;         // int32 words before the entries (
 constexpr int kPlanPer = 8;                  // plan entries per block
 
 template <int TYPE>
-__global__ void __launch_bounds__(kHarmThreads) harmonic_planned_kernel(const HarmArgs A,
+__global__ void __launch_bounds__(kHarmThreads, 6) harmonic_planned_kernel(const HarmArgs A,
                                                                        const int32_t* hdr) {
     const int64_t width = (int64_t)(uint32_t)hdr[3] | ((int64_t)hdr[4] << 32);
     if (hdr[0] != kPlanMagic || hdr[1] != A.K || hdr[2] != A.j0h || width != A.width) {
