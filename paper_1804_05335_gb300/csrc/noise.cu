@@ -9,33 +9,46 @@
 //   half bin      (pi/4)(F_r - F_{r+1}):    (pi/4)^2 sum_d |Rt(d) - Rt(d-1)|^2,
 //                 Rt = R on |d| <= h and 0 outside
 //   half-integer  F(r + 1/2) (2-bin interpolation):    sum_{|d|<=h, d in Z+1/2} |R(d)|^2
-// One warp per plane row sums over the taps in FP64 (R from fresnel.cuh).
+// One CTA per plane row evaluates, one per thread, the 2h + 1 responses at
+// integer offsets (kept in shared memory for the half-bin differences) and
+// the 2h at half-integer ones, in FP64 (R from fresnel.cuh), then reduces the
+// three sums across its warps.
 #include "fresnel.cuh"
 #include "internal.h"
 
 namespace fdas {
 
-__global__ void noise_means_kernel(int zmin, int zstep, int K, int interbin, float* __restrict__ out) {
-    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= K) return;
+constexpr int kNoiseThreads = 512;
+
+__global__ void __launch_bounds__(kNoiseThreads) noise_means_kernel(int zmin, int zstep, int K,
+                                                                    int interbin,
+                                                                    float* __restrict__ out) {
+    extern __shared__ double2 rs[];   // Rt(d) at rs[d + h + 1], d = -h-1 .. h+1
+    __shared__ double part[3][kNoiseThreads / 32];
+    const int row = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int z = zmin + row * zstep;
     const int az = z < 0 ? -z : z;
     const int h = (az + 1) / 2 + 8;
+    const int nint = 2 * h + 1;
     double e_full = 0.0, e_half = 0.0, e_mid = 0.0;
-    for (int d = -h + lane; d <= h + 1; d += 32) {
-        // Rt(d) and Rt(d - 1) (zero outside the window), R(d - 1/2)
-        const cd r0 = (d <= h) ? response<double>((double)z, (double)d) : cd{0.0, 0.0};
-        const cd r1 = (d - 1 >= -h) ? response<double>((double)z, (double)(d - 1)) : cd{0.0, 0.0};
-        if (d <= h) e_full += r0.x * r0.x + r0.y * r0.y;
-        const double dx = r0.x - r1.x, dy = r0.y - r1.y;
-        e_half += dx * dx + dy * dy;
-        if (d <= h) {   // half-integer offset d - 1/2 inside the window: |d - 1/2| <= h - 1/2
-            if (d - 1 >= -h) {
-                const cd rm = response<double>((double)z, (double)d - 0.5);
-                e_mid += rm.x * rm.x + rm.y * rm.y;
-            }
+    for (int i = threadIdx.x; i < nint + 2 * h; i += kNoiseThreads) {
+        if (i < nint) {   // integer offset d = i - h
+            const cd r = response<double>((double)z, (double)(i - h));
+            rs[i + 1] = make_double2(r.x, r.y);
+            e_full += r.x * r.x + r.y * r.y;
+        } else {          // half-integer offset d - 1/2, d = -h+1 .. h
+            const cd r = response<double>((double)z, (double)(i - nint - h + 1) - 0.5);
+            e_mid += r.x * r.x + r.y * r.y;
         }
+    }
+    if (threadIdx.x == 0) rs[0] = make_double2(0.0, 0.0);           // Rt(-h-1)
+    if (threadIdx.x == 1) rs[2 * h + 2] = make_double2(0.0, 0.0);   // Rt(h+1)
+    __syncthreads();
+    for (int d = -h + (int)threadIdx.x; d <= h + 1; d += kNoiseThreads) {
+        const double2 a = rs[d + h + 1], b = rs[d + h];   // Rt(d), Rt(d - 1)
+        const double dx = a.x - b.x, dy = a.y - b.y;
+        e_half += dx * dx + dy * dy;
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -44,6 +57,18 @@ __global__ void noise_means_kernel(int zmin, int zstep, int K, int interbin, flo
         e_mid += __shfl_xor_sync(0xffffffffu, e_mid, o);
     }
     if (lane == 0) {
+        part[0][warp] = e_full;
+        part[1][warp] = e_half;
+        part[2][warp] = e_mid;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        e_full = e_half = e_mid = 0.0;
+        for (int w = 0; w < kNoiseThreads / 32; ++w) {
+            e_full += part[0][w];
+            e_half += part[1][w];
+            e_mid += part[2][w];
+        }
         const double hs = 0.61685027506808491;   // (pi/4)^2
         out[2 * row] = (float)e_full;
         out[2 * row + 1] = (float)(interbin == 1 ? hs * e_half : interbin == 2 ? e_mid : e_full);
@@ -59,8 +84,8 @@ extern "C" int fdas_noise_means(const fdas_params* p, float* means, void* stream
     int rc = make_grid(p, &g);
     if (rc != FDAS_OK) return rc;
     if (!means || !aligned(means, 4)) return FDAS_E_INVAL;
-    constexpr int kWarps = 4;
-    noise_means_kernel<<<(g.K + kWarps - 1) / kWarps, 32 * kWarps, 0, (cudaStream_t)stream>>>(
-        p->zmin, p->zstep, g.K, p->interbin, means);
+    const size_t sm = (size_t)(2 * g.hmax + 3) * sizeof(double2);   // <= 32.8 KB (h <= 1023)
+    noise_means_kernel<<<g.K, kNoiseThreads, sm, (cudaStream_t)stream>>>(p->zmin, p->zstep, g.K,
+                                                                           p->interbin, means);
     return cuda_status(cudaGetLastError());
 }
